@@ -1,0 +1,183 @@
+/*
+ * lqdd.h -- C ABI of the GB300 (sm_103a) odd-even Wilson-clover library.
+ *
+ * The library computes the finest-level, data-parallel part of DD-alpha-AMG
+ * as described in arxiv 2407.08092: the odd-even (Schur-complement)
+ * preconditioned Wilson-clover Dirac operator (Sec. 2.3, Sec. 2.4.5, Eq. 1-3),
+ * the Richardson and GMRES smoothers built on it (Algorithms 2 and 4,
+ * Sec. 2.4.5) and an odd-even (F)GMRES solve to a relative residual (Sec. 2.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Operator.  (D psi)(x) = C(x) psi(x) - 1/2 sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                      + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu) ]
+ *   C(x) = (4 + m0) + c_sw (i/4) sum_{mu,nu} sigma_mu_nu F_mu_nu(x), sigma_mu_nu =
+ *   (i/2)[g_mu, g_nu], F_mu_nu = (Q_mu_nu - Q_mu_nu^+)/8 with Q the sum of the four
+ *   plaquette leaves at x.  Chiral gamma basis: g_k = [[0,-i s_k],[i s_k,0]],
+ *   g_4 = [[0,1],[1,0]], g_5 = diag(1,1,-1,-1); C(x) is two 6x6 blocks (spins
+ *   {0,1} and {2,3}).  Space is periodic; hops across the time boundary are
+ *   multiplied by lq_lattice.t_bc.
+ * Lattice.  L = {Lx, Ly, Lz, Lt}, every extent even and >= 2.  Natural site
+ *   order is lexicographic with x fastest: lex = x + Lx*(y + Ly*(z + Lz*t)).
+ *   A site is even iff x+y+z+t is even (Sec. 2.4.5).
+ * Fields (caller-owned DEVICE memory unless stated; complex double, i.e.
+ *   interleaved re/im doubles, 16-byte aligned):
+ *   gauge       U[V][4][3][3]   U[x][mu][a][b] = row a, column b of U_mu(x)
+ *   full spinor psi[V][4][3]    spin, then colour
+ *   half spinor psi[V/2][4][3]  the sites of one parity in lexicographic order
+ *                               (entry i is the site with lex/2 == i)
+ *   The library keeps its own internal copies in a checkerboarded,
+ *   structure-of-arrays layout; that layout never crosses this boundary.
+ * Streams.  Every call enqueues its work on the stream given to lq_create and
+ *   returns without a device synchronisation, except where a call returns host
+ *   scalars (lq_set_gauge, lq_estimate_norm, lq_norm2, lq_solve, lq_smooth with a
+ *   GMRES smoother): those synchronise the stream before returning.
+ * Errors.  Every call returns an lq_status; nothing aborts, traps or throws
+ *   across this boundary.  lq_last_error() describes the most recent failure
+ *   of a context.  A failed call leaves output buffers unspecified.
+ * Ownership.  The library owns the context, its internal field copies and
+ *   the Krylov workspace (allocated on first use, sized by the restart
+ *   length, freed by lq_destroy).  The caller owns every buffer it passes.
+ */
+#ifndef LQDD_H
+#define LQDD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lq_ctx lq_ctx;
+
+typedef enum {
+    LQ_OK = 0,
+    LQ_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad enum) */
+    LQ_ERR_CUDA = 2,           /* a CUDA runtime call failed; see lq_last_error */
+    LQ_ERR_OOM = 3,            /* device or pinned-host allocation failed */
+    LQ_ERR_NOT_CONVERGED = 4,  /* tolerance not reached within max_restarts; x is the last iterate */
+    LQ_ERR_BREAKDOWN = 5,      /* a clover block is not invertible (non-positive LDL pivot) */
+    LQ_ERR_NAN = 6,            /* a NaN or Inf appeared in a residual or norm */
+    LQ_ERR_STATE = 7           /* call out of order (e.g. an operator before lq_set_gauge) */
+} lq_status;
+
+typedef enum { LQ_F64 = 0, LQ_F32 = 1 } lq_prec;
+
+typedef enum {
+    LQ_OP_FULL = 0,      /* D on the full lattice: in, out are full spinors */
+    LQ_OP_SCHUR = 1,     /* D_S = D_ee - D_eo D_oo^{-1} D_oe (Eq. 3): even half spinors */
+    LQ_OP_SCHUR_DAG = 2, /* D_S^+ = g5 D_S g5: even half spinors */
+    LQ_OP_EE = 3,        /* D_ee = C on even sites: even half spinors */
+    LQ_OP_OO_INV = 4     /* D_oo^{-1} = C^{-1} on odd sites: odd half spinors */
+} lq_op;
+
+typedef enum { LQ_SOLVER_GMRES = 0, LQ_SOLVER_FGMRES = 1 } lq_solver_kind;
+typedef enum { LQ_SMOOTH_NONE = 0, LQ_SMOOTH_RICHARDSON = 1, LQ_SMOOTH_GMRES = 2 } lq_smoother_kind;
+
+typedef struct {
+    int L[4];      /* Lx, Ly, Lz, Lt: even, >= 2 */
+    int t_bc;      /* +1 periodic or -1 antiperiodic in time (fermion hops only) */
+    double m0;     /* bare mass: the site diagonal is 4 + m0 */
+    double csw;    /* clover coefficient c_sw (Table 5 lists the paper's value) */
+} lq_lattice;
+
+typedef struct {
+    int solver;          /* lq_solver_kind.  GMRES(m) on D_S (Algorithm 2), or flexible GMRES(m)
+                            in FP64 right-preconditioned by the smoother (the outer solver of
+                            Sec. 2.3) */
+    int prec;            /* lq_prec of a plain GMRES solve (ignored by FGMRES, whose outer
+                            iteration is always FP64) */
+    double tol;          /* stop when ||b_hat_e - D_S x_e|| <= tol ||b_hat_e|| (recomputed) */
+    int restart;         /* Krylov length m of each cycle, 1..256 */
+    int max_restarts;    /* maximum number of cycles, >= 1 */
+    int smoother;        /* lq_smoother_kind: preconditioner of FGMRES, or the method of lq_smooth */
+    int smooth_n;        /* Richardson sweeps n, or GMRES(n, m) cycles n */
+    int smooth_m;        /* GMRES(n, m) cycle length m, 1..256 */
+    double omega;        /* Richardson weight omega = delta / |lambda_max(D_S)| (Algorithm 4) */
+    double smooth_tol;   /* GMRES smoother: also stop once its relative residual <= smooth_tol
+                            (0 runs exactly n cycles of m steps) */
+    int inner_prec;      /* lq_prec of the smoother / preconditioner */
+} lq_solver_params;
+
+typedef struct {
+    int cycles;              /* restart cycles of the (outer) solver */
+    int iters;               /* Arnoldi steps of the (outer) solver */
+    long long inner_iters;   /* D_S applications inside smoother / preconditioner calls */
+    double rel_resid;        /* ||b_hat_e - D_S x_e|| / ||b_hat_e|| at exit, recomputed in FP64 */
+    double rel_resid_true;   /* ||b - D x|| / ||b|| on the full lattice, FP64 */
+    double time_ms;          /* host wall time of the call */
+    double bytes;            /* algorithmic bytes of every kernel the call launched */
+    long long launches;      /* kernels the call launched */
+} lq_stats;
+
+/* Create a context for one lattice on the current CUDA device.  `stream` is a
+ * cudaStream_t (NULL: the legacy default stream).  *out receives the context. */
+lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream);
+
+/* Release the context and all library-owned device and host memory. */
+lq_status lq_destroy(lq_ctx *ctx);
+
+/* Load a gauge field (device U[V][4][3][3], complex double, natural order) and
+ * build from it, on the device: the internal FP64 and FP32 link copies, the
+ * clover term C(x) of every site (Sec. 2.3) and the inverse D_oo^{-1} of the odd
+ * blocks (6x6 Hermitian blocks, Sec. 2.4.5).  Links are expected to be SU(3);
+ * the FP32 copy keeps two rows and rebuilds the third as conj(r1 x r2).
+ * Synchronises; LQ_ERR_BREAKDOWN if a clover block has a non-positive pivot. */
+lq_status lq_set_gauge(lq_ctx *ctx, const void *U);
+
+/* out = op(in) in precision `prec` (lq_prec): the data are read as complex
+ * double, converted to the internal layout of that precision, the operator is
+ * applied there and the result converted back.  Field sizes per lq_op. */
+lq_status lq_apply(lq_ctx *ctx, int op, int prec, const void *in, void *out);
+
+/* Right factor of Eq. 2: bhat_e = b_e - D_eo D_oo^{-1} b_o.
+ * b: full spinor; bhat_e: even half spinor.  FP64. */
+lq_status lq_prepare(lq_ctx *ctx, const void *b, void *bhat_e);
+
+/* Left factor of Eq. 2: x_o = D_oo^{-1} (b_o - D_oe x_e); writes the full x
+ * (even part = x_e).  b, x: full spinors; x_e: even half spinor.  FP64. */
+lq_status lq_reconstruct(lq_ctx *ctx, const void *b, const void *x_e, void *x);
+
+/* Power iteration on D_S^+ D_S (Sec. 2.4.4): v = v0/||v0||, then `iters` times
+ * w = D_S^+ D_S v, lam = ||w||, v = w/lam; *out = sqrt(lam), an estimate of
+ * ||D_S||_2 >= |lambda_max(D_S)| from below.  v0: even half spinor (device).
+ * FP64.  Synchronises. */
+lq_status lq_estimate_norm(lq_ctx *ctx, int iters, const void *v0, double *out);
+
+/* *out = ||v||^2 for a device field of n_sites sites x 12 complex doubles.
+ * Deterministic two-stage FP64 reduction.  Synchronises. */
+lq_status lq_norm2(lq_ctx *ctx, const void *v, long long n_sites, double *out);
+
+/* The odd-even smoother e = M_n r of Sec. 2.4.5 / Fig. 1: Eq. 2 with D_S^{-1}
+ * replaced by `smooth_n` Richardson sweeps (weight omega, Algorithm 4) or by
+ * GMRES(smooth_n, smooth_m) (Algorithm 2), started from zero, run in
+ * params->inner_prec.  r, e: full spinors. */
+lq_status lq_smooth(lq_ctx *ctx, const lq_solver_params *params, const void *r, void *e);
+
+/* Solve D x = b by odd-even reduction (Eq. 2): prepare, solve the Schur system
+ * with the method in params, reconstruct.  x holds the initial guess on entry
+ * (its even half starts the iteration; pass zeros for none) and the solution on
+ * exit.  b, x: full spinors.  stats may be NULL.  Synchronises.
+ * LQ_ERR_NOT_CONVERGED still writes the last iterate and fills stats. */
+lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, void *x,
+                   lq_stats *stats);
+
+/* Copy the clover blocks out for inspection: which = 0 gives C(x), which = 1
+ * gives C(x)^{-1} (odd sites only; even entries are zero).  out: device
+ * complex double [V][2][6][6], natural site order, block 0 = spins {0,1},
+ * block 1 = spins {2,3}, index (spin%2)*3 + colour. */
+lq_status lq_export_clover(lq_ctx *ctx, int which, void *out);
+
+/* Counters since the context was created: kernels launched and their
+ * algorithmic bytes.  Either pointer may be NULL. */
+lq_status lq_counters(lq_ctx *ctx, long long *launches, double *bytes);
+
+/* A static description of the last failure on this context ("" if none). */
+const char *lq_last_error(lq_ctx *ctx);
+
+/* A static name for a status code. */
+const char *lq_status_string(lq_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQDD_H */

@@ -1,0 +1,877 @@
+// C-ABI entry points, the library context and the host-side solver drivers.
+//
+// Solvers (host control flow, device arithmetic):
+//  * GMRES(m) on D_S (Algorithm 2).  The Arnoldi step orthogonalises with
+//    classical Gram-Schmidt applied twice (CGS2: one fused multi-dot and one
+//    multi-axpy per pass, both over the whole basis) instead of the listing's
+//    modified Gram-Schmidt, so that each pass is one sweep over memory; the
+//    Hessenberg least-squares problem is solved by Givens rotations on the host.
+//  * Flexible GMRES(m) in FP64 (the outer solver of every level, Sec. 2.3),
+//    right-preconditioned by a Richardson or GMRES smoother in FP64 or FP32.
+//  * Richardson(n) on D_S (Algorithm 4) with the update fused into the second
+//    hopping kernel; the first sweep from x = 0 is x = omega b.
+//  * The odd-even smoother M_n (Sec. 2.4.5): prepare, smoother on D_S,
+//    reconstruct (Eq. 2).
+//  * Power iteration on D_S^+ D_S for ||D_S||_2 (Sec. 2.4.4).
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lqdd.h"
+#include "lq_kernels.h"
+
+using namespace lq;
+typedef std::complex<double> cd;
+
+static constexpr int MAX_RESTART = 256;
+static constexpr int RED_SLOTS = 2 * MAX_RESTART + 8;
+
+struct lq_ctx {
+    Geom g;
+    lq_lattice lat;
+    cudaStream_t st;
+    Counters ctr;
+    int device;
+    bool have_gauge = false;
+    void *U64[2] = {nullptr, nullptr};
+    void *U32[2] = {nullptr, nullptr};
+    void *C64[2] = {nullptr, nullptr};
+    void *C32[2] = {nullptr, nullptr};
+    void *Ci64 = nullptr;
+    void *Ci32 = nullptr;
+    int *dflag = nullptr;
+    RedScratch red{};
+    double *h_pin = nullptr;   // pinned host mirror of red.out / coefficients
+    double *d_coef = nullptr;  // device coefficients [2 * RED_SLOTS]
+    std::map<std::string, std::pair<void *, size_t>> ws;
+    std::vector<void *> owned;
+    std::string err;
+    Exec ex() { return Exec{g, st, &ctr}; }
+};
+
+namespace {
+
+struct Fail {
+    lq_status s;
+};
+
+void fail(lq_ctx *c, lq_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    throw Fail{s};
+}
+
+void ck(lq_ctx *c, cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, e == cudaErrorMemoryAllocation ? LQ_ERR_OOM : LQ_ERR_CUDA,
+             std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void ck_launch(lq_ctx *c, const char *what) { ck(c, cudaGetLastError(), what); }
+
+void *dev_alloc(lq_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    ck(c, cudaMalloc(&p, bytes), "cudaMalloc");
+    c->owned.push_back(p);
+    return p;
+}
+
+// named, grow-only workspace buffer
+void *ws(lq_ctx *c, const std::string &name, size_t bytes)
+{
+    auto it = c->ws.find(name);
+    if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;
+    if (it != c->ws.end()) {
+        cudaFree(it->second.first);
+        for (auto &p : c->owned)
+            if (p == it->second.first) p = nullptr;
+        c->ws.erase(it);
+    }
+    void *p = dev_alloc(c, bytes);
+    c->ws[name] = {p, bytes};
+    return p;
+}
+
+void *field(lq_ctx *c, int prec, const char *name)
+{
+    return ws(c, std::string(name) + (prec == P64 ? "/64" : "/32"), spinor_bytes(c->g, prec));
+}
+
+void *basis(lq_ctx *c, int prec, const char *name, int n)
+{
+    return ws(c, std::string(name) + (prec == P64 ? "/64" : "/32"), (size_t)n * spinor_bytes(c->g, prec));
+}
+
+inline void *vec_at(lq_ctx *c, int prec, void *base, int j)
+{
+    return (char *)base + (size_t)j * spinor_bytes(c->g, prec);
+}
+
+void sync(lq_ctx *c) { ck(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize"); }
+
+// copy r.out[first .. first+count) (complex slots) to the pinned mirror and wait
+const double *fetch(lq_ctx *c, int first, int count)
+{
+    ck(c, cudaMemcpyAsync(c->h_pin + 2 * first, c->red.out + 2 * first, sizeof(double) * 2 * count,
+                          cudaMemcpyDeviceToHost, c->st),
+       "cudaMemcpyAsync D2H");
+    sync(c);
+    return c->h_pin + 2 * first;
+}
+
+double norm2_of(lq_ctx *c, int prec, const void *v)
+{
+    Exec e = c->ex();
+    norm2(e, prec, v, c->red, 0);
+    reduce_finish(e, c->red, 0, 1);
+    ck_launch(c, "norm2");
+    return fetch(c, 0, 1)[0];
+}
+
+void need_gauge(lq_ctx *c)
+{
+    if (!c->have_gauge) fail(c, LQ_ERR_STATE, "no gauge field: call lq_set_gauge first");
+}
+
+const void *Cp(lq_ctx *c, int prec, int parity) { return prec == P64 ? c->C64[parity] : c->C32[parity]; }
+const void *Cip(lq_ctx *c, int prec) { return prec == P64 ? c->Ci64 : c->Ci32; }
+
+HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
+{
+    HopCall h{};
+    h.mode = mode;
+    h.prec = prec;
+    h.pout = pout;
+    h.U[0] = prec == P64 ? c->U64[0] : c->U32[0];
+    h.U[1] = prec == P64 ? c->U64[1] : c->U32[1];
+    return h;
+}
+
+// ---- operators on internal fields ---------------------------------------------
+
+// out_e = D_S in_e (Eq. 3) via K1 (odd sites) and K2 (even sites); t: odd temporary
+void op_schur(lq_ctx *c, int prec, const void *in, void *out, void *t)
+{
+    Exec e = c->ex();
+    HopCall k1 = hopcall(c, HOP_K1, prec, 1);
+    k1.in = in;
+    k1.out = t;
+    k1.clov = Cip(c, prec);
+    hop(e, k1);
+    HopCall k2 = hopcall(c, HOP_K2, prec, 0);
+    k2.in = t;
+    k2.in2 = in;
+    k2.out = out;
+    k2.clov = Cp(c, prec, 0);
+    hop(e, k2);
+}
+
+// x_e += omega (b_e - D_S x_e), fused into K2
+void op_rich_sweep(lq_ctx *c, int prec, void *x, const void *b, double omega, void *t)
+{
+    Exec e = c->ex();
+    HopCall k1 = hopcall(c, HOP_K1, prec, 1);
+    k1.in = x;
+    k1.out = t;
+    k1.clov = Cip(c, prec);
+    hop(e, k1);
+    HopCall k2 = hopcall(c, HOP_RICH, prec, 0);
+    k2.in = t;
+    k2.in2 = x;
+    k2.b = b;
+    k2.out = x;
+    k2.clov = Cp(c, prec, 0);
+    k2.omega = omega;
+    hop(e, k2);
+}
+
+void op_full(lq_ctx *c, int prec, const void *ie, const void *io, void *oe, void *oo)
+{
+    Exec e = c->ex();
+    HopCall a = hopcall(c, HOP_FULL, prec, 0);
+    a.in = io;
+    a.in2 = ie;
+    a.out = oe;
+    a.clov = Cp(c, prec, 0);
+    hop(e, a);
+    HopCall b = hopcall(c, HOP_FULL, prec, 1);
+    b.in = ie;
+    b.in2 = io;
+    b.out = oo;
+    b.clov = Cp(c, prec, 1);
+    hop(e, b);
+}
+
+// bhat_e = b_e - D_eo D_oo^{-1} b_o
+void op_prepare(lq_ctx *c, int prec, const void *be, const void *bo, void *bhat, void *t)
+{
+    Exec e = c->ex();
+    clover_mul(e, prec, Cip(c, prec), bo, t);
+    HopCall p = hopcall(c, HOP_PREP, prec, 0);
+    p.in = t;
+    p.in2 = be;
+    p.out = bhat;
+    hop(e, p);
+}
+
+// x_o = D_oo^{-1} (b_o - D_oe x_e)
+void op_reconstruct(lq_ctx *c, int prec, const void *bo, const void *xe, void *xo)
+{
+    Exec e = c->ex();
+    HopCall r = hopcall(c, HOP_RECON, prec, 1);
+    r.in = xe;
+    r.in2 = bo;
+    r.out = xo;
+    r.clov = Cip(c, prec);
+    hop(e, r);
+}
+
+// ---- Krylov solvers ---------------------------------------------------------------
+
+struct KResult {
+    int cycles = 0;
+    int iters = 0;
+    double relres = 0.0;   // last residual estimate or recomputed value, relative to ||b||
+    bool converged = false;
+};
+
+// Givens-rotation least squares of the Arnoldi relation, on the host
+struct Hess {
+    int m;
+    std::vector<cd> H;   // column-major (m+1) x m
+    std::vector<double> cs;
+    std::vector<cd> sn;
+    std::vector<cd> gv;
+    explicit Hess(int m_) : m(m_), H((size_t)(m_ + 1) * m_), cs(m_), sn(m_), gv(m_ + 1) {}
+    cd &h(int i, int j) { return H[(size_t)j * (m + 1) + i]; }
+    void reset(double beta)
+    {
+        std::fill(gv.begin(), gv.end(), cd(0));
+        gv[0] = beta;
+    }
+    // rotate column k (entries 0..k+1 already stored); returns |g_{k+1}|
+    double rotate(int k)
+    {
+        for (int i = 0; i < k; i++) {
+            cd a = h(i, k), b = h(i + 1, k);
+            h(i, k) = cs[i] * a + sn[i] * b;
+            h(i + 1, k) = -std::conj(sn[i]) * a + cs[i] * b;
+        }
+        cd a = h(k, k), b = h(k + 1, k);
+        double t = std::sqrt(std::norm(a) + std::norm(b));
+        if (std::abs(a) == 0.0) {
+            cs[k] = 0.0;
+            sn[k] = 1.0;
+        } else {
+            cs[k] = std::abs(a) / t;
+            sn[k] = (a / std::abs(a)) * std::conj(b) / t;
+        }
+        h(k, k) = cs[k] * a + sn[k] * b;
+        h(k + 1, k) = 0.0;
+        cd gk = gv[k];
+        gv[k] = cs[k] * gk;
+        gv[k + 1] = -std::conj(sn[k]) * gk;
+        return std::abs(gv[k + 1]);
+    }
+    // back-substitution R y = g for the first n columns
+    std::vector<cd> solve(int n)
+    {
+        std::vector<cd> y(n);
+        for (int i = n - 1; i >= 0; i--) {
+            cd acc = gv[i];
+            for (int j = i + 1; j < n; j++) acc -= h(i, j) * y[j];
+            y[i] = acc / h(i, i);
+        }
+        return y;
+    }
+};
+
+void upload_coef(lq_ctx *c, const std::vector<cd> &y)
+{
+    for (size_t j = 0; j < y.size(); j++) {
+        c->h_pin[2 * RED_SLOTS + 2 * j] = y[j].real();
+        c->h_pin[2 * RED_SLOTS + 2 * j + 1] = y[j].imag();
+    }
+    ck(c, cudaMemcpyAsync(c->d_coef, c->h_pin + 2 * RED_SLOTS, sizeof(double) * 2 * y.size(), cudaMemcpyHostToDevice,
+                          c->st),
+       "cudaMemcpyAsync H2D");
+    // the pinned staging area is reused by the next upload: wait for this copy
+    sync(c);
+}
+
+// Arnoldi step: w <- w orthogonalised against V[0..k] by CGS2; returns the
+// Hessenberg column h[0..k] and h_{k+1,k} = ||w|| (not yet normalised)
+double arnoldi_cgs2(lq_ctx *c, int prec, void *V, int k, void *w, Hess &H)
+{
+    Exec e = c->ex();
+    const int n = k + 1;
+    multi_dot(e, prec, V, n, w, c->red, 0);
+    reduce_finish(e, c->red, 0, n);
+    multi_axpy(e, prec, V, n, c->red.out, -1, w, nullptr, 0);
+    multi_dot(e, prec, V, n, w, c->red, n);
+    reduce_finish(e, c->red, n, n);
+    multi_axpy(e, prec, V, n, c->red.out + 2 * n, -1, w, &c->red, 2 * n);
+    reduce_finish(e, c->red, 2 * n, 1);
+    ck_launch(c, "arnoldi");
+    const double *hv = fetch(c, 0, 2 * n + 1);
+    for (int j = 0; j < n; j++) H.h(j, k) = cd(hv[2 * j] + hv[2 * (n + j)], hv[2 * j + 1] + hv[2 * (n + j) + 1]);
+    const double nrm2 = hv[4 * n];
+    if (!std::isfinite(nrm2)) fail(c, LQ_ERR_NAN, "NaN/Inf in the Arnoldi process");
+    return std::sqrt(nrm2);
+}
+
+// Restarted GMRES(m) on D_S in precision `prec`: b, x internal even fields.
+// x_zero: x is known to be zero on entry (skips the first residual product).
+// tol > 0 stops at ||b - D_S x|| <= tol ||b||; tol == 0 runs max_cycles full cycles.
+KResult gmres(lq_ctx *c, int prec, const void *b, void *x, int m, int max_cycles, double tol, bool x_zero,
+              const char *wsname, double bnorm_hint = -1.0)
+{
+    Exec e = c->ex();
+    KResult R;
+    void *V = basis(c, prec, wsname, m + 1);
+    void *t = field(c, prec, (std::string(wsname) + ":t").c_str());
+    const double bnorm = bnorm_hint >= 0 ? bnorm_hint : std::sqrt(norm2_of(c, prec, b));
+    if (!std::isfinite(bnorm)) fail(c, LQ_ERR_NAN, "NaN/Inf in the right-hand side");
+    if (bnorm == 0.0) {
+        zero(e, prec, x);
+        R.converged = true;
+        return R;
+    }
+    Hess H(m);
+    for (int cyc = 0; cyc < max_cycles; cyc++) {
+        void *v0 = vec_at(c, prec, V, 0);
+        double beta;
+        if (x_zero) {
+            copy(e, prec, b, v0);
+            beta = bnorm;
+        } else {
+            op_schur(c, prec, x, v0, t);
+            axpby(e, prec, 1.0, 0.0, b, -1.0, 0.0, v0);   // v0 = b - D_S x
+            beta = std::sqrt(norm2_of(c, prec, v0));
+            if (!std::isfinite(beta)) fail(c, LQ_ERR_NAN, "NaN/Inf in the residual");
+        }
+        R.relres = beta / bnorm;
+        if (tol > 0 && beta <= tol * bnorm) {
+            R.converged = true;
+            return R;
+        }
+        R.cycles++;
+        axpby(e, prec, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
+        H.reset(beta);
+        int nk = 0;
+        for (int k = 0; k < m; k++) {
+            void *w = vec_at(c, prec, V, k + 1);
+            op_schur(c, prec, vec_at(c, prec, V, k), w, t);
+            const double hk1 = arnoldi_cgs2(c, prec, V, k, w, H);
+            double colnorm2 = hk1 * hk1;
+            for (int j = 0; j <= k; j++) colnorm2 += std::norm(H.h(j, k));
+            H.h(k + 1, k) = hk1;
+            const double est = H.rotate(k);
+            nk = k + 1;
+            R.iters++;
+            R.relres = est / bnorm;
+            const bool breakdown = hk1 <= 1e-14 * std::sqrt(colnorm2);
+            if (breakdown || (tol > 0 && est <= tol * bnorm) || k == m - 1) break;
+            axpby(e, prec, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
+        }
+        std::vector<cd> y = H.solve(nk);
+        upload_coef(c, y);
+        multi_axpy(e, prec, V, nk, c->d_coef, +1, x, nullptr, 0);
+        ck_launch(c, "gmres update");
+        x_zero = false;
+        if (tol > 0 && R.relres <= tol) {
+            // confirm with the recomputed residual before declaring convergence
+            continue;
+        }
+    }
+    if (tol > 0) {
+        void *r = vec_at(c, prec, V, 0);
+        op_schur(c, prec, x, r, t);
+        axpby(e, prec, 1.0, 0.0, b, -1.0, 0.0, r);
+        R.relres = std::sqrt(norm2_of(c, prec, r)) / bnorm;
+        R.converged = R.relres <= tol;
+    }
+    return R;
+}
+
+// Richardson(n) from x = 0 on D_S in precision prec (Algorithm 4)
+void richardson(lq_ctx *c, int prec, const void *b, void *x, int n, double omega, const char *wsname)
+{
+    Exec e = c->ex();
+    if (n <= 0) {
+        zero(e, prec, x);
+        return;
+    }
+    void *t = field(c, prec, (std::string(wsname) + ":t").c_str());
+    axpby(e, prec, omega, 0.0, b, 0.0, 0.0, x);   // first sweep: x = 0 + omega (b - D_S 0)
+    for (int i = 1; i < n; i++) op_rich_sweep(c, prec, x, b, omega, t);
+}
+
+// the preconditioner / smoother on D_S: z = M v, both in precision q
+long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void *v, void *z)
+{
+    if (p->smoother == LQ_SMOOTH_RICHARDSON) {
+        richardson(c, q, v, z, p->smooth_n, p->omega, "rich");
+        return p->smooth_n;
+    }
+    if (p->smoother == LQ_SMOOTH_GMRES) {
+        Exec e = c->ex();
+        zero(e, q, z);
+        KResult r = gmres(c, q, v, z, p->smooth_m, p->smooth_n, p->smooth_tol, true, "inner");
+        return r.iters;
+    }
+    copy(c->ex(), q, v, z);
+    return 0;
+}
+
+// Flexible GMRES(m) in FP64, right-preconditioned by the smoother in inner_prec
+KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, long long *inner_iters)
+{
+    Exec e = c->ex();
+    KResult R;
+    const int m = p->restart;
+    const int q = p->inner_prec;
+    void *V = basis(c, P64, "outerV", m + 1);
+    void *Z = basis(c, P64, "outerZ", m);
+    void *t = field(c, P64, "outer:t");
+    void *vq = q == P64 ? nullptr : field(c, q, "prec:v");
+    void *zq = q == P64 ? nullptr : field(c, q, "prec:z");
+    const double bnorm = std::sqrt(norm2_of(c, P64, b));
+    if (!std::isfinite(bnorm)) fail(c, LQ_ERR_NAN, "NaN/Inf in the right-hand side");
+    if (bnorm == 0.0) {
+        zero(e, P64, x);
+        R.converged = true;
+        return R;
+    }
+    Hess H(m);
+    for (int cyc = 0; cyc < p->max_restarts; cyc++) {
+        void *v0 = vec_at(c, P64, V, 0);
+        op_schur(c, P64, x, v0, t);
+        axpby(e, P64, 1.0, 0.0, b, -1.0, 0.0, v0);
+        const double beta = std::sqrt(norm2_of(c, P64, v0));
+        if (!std::isfinite(beta)) fail(c, LQ_ERR_NAN, "NaN/Inf in the residual");
+        R.relres = beta / bnorm;
+        if (beta <= p->tol * bnorm) {
+            R.converged = true;
+            return R;
+        }
+        R.cycles++;
+        axpby(e, P64, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
+        H.reset(beta);
+        int nk = 0;
+        for (int k = 0; k < m; k++) {
+            void *vk = vec_at(c, P64, V, k);
+            void *zk = vec_at(c, P64, Z, k);
+            if (q == P64) {
+                *inner_iters += smoother_schur(c, p, P64, vk, zk);
+            } else {
+                convert(e, P64, vk, q, vq);
+                *inner_iters += smoother_schur(c, p, q, vq, zq);
+                convert(e, q, zq, P64, zk);
+            }
+            void *w = vec_at(c, P64, V, k + 1);
+            op_schur(c, P64, zk, w, t);
+            const double hk1 = arnoldi_cgs2(c, P64, V, k, w, H);
+            double colnorm2 = hk1 * hk1;
+            for (int j = 0; j <= k; j++) colnorm2 += std::norm(H.h(j, k));
+            H.h(k + 1, k) = hk1;
+            const double est = H.rotate(k);
+            nk = k + 1;
+            R.iters++;
+            R.relres = est / bnorm;
+            const bool breakdown = hk1 <= 1e-14 * std::sqrt(colnorm2);
+            if (breakdown || est <= p->tol * bnorm || k == m - 1) break;
+            axpby(e, P64, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
+        }
+        std::vector<cd> y = H.solve(nk);
+        upload_coef(c, y);
+        multi_axpy(e, P64, Z, nk, c->d_coef, +1, x, nullptr, 0);
+        ck_launch(c, "fgmres update");
+    }
+    void *r = vec_at(c, P64, V, 0);
+    op_schur(c, P64, x, r, t);
+    axpby(e, P64, 1.0, 0.0, b, -1.0, 0.0, r);
+    R.relres = std::sqrt(norm2_of(c, P64, r)) / bnorm;
+    R.converged = R.relres <= p->tol;
+    return R;
+}
+
+void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
+{
+    if (!p) fail(c, LQ_ERR_ARG, "params is NULL");
+    if (solve) {
+        if (p->solver != LQ_SOLVER_GMRES && p->solver != LQ_SOLVER_FGMRES) fail(c, LQ_ERR_ARG, "bad solver");
+        if (p->restart < 1 || p->restart > MAX_RESTART) fail(c, LQ_ERR_ARG, "restart out of range 1..256");
+        if (p->max_restarts < 1) fail(c, LQ_ERR_ARG, "max_restarts < 1");
+        if (!(p->tol > 0.0) || !std::isfinite(p->tol)) fail(c, LQ_ERR_ARG, "tol must be positive");
+        if (p->prec != LQ_F64 && p->prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad prec");
+    }
+    if (p->smoother < LQ_SMOOTH_NONE || p->smoother > LQ_SMOOTH_GMRES) fail(c, LQ_ERR_ARG, "bad smoother");
+    if (p->inner_prec != LQ_F64 && p->inner_prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad inner_prec");
+    if (p->smoother != LQ_SMOOTH_NONE && p->smooth_n < 0) fail(c, LQ_ERR_ARG, "smooth_n < 0");
+    if (p->smoother == LQ_SMOOTH_GMRES && (p->smooth_m < 1 || p->smooth_m > MAX_RESTART))
+        fail(c, LQ_ERR_ARG, "smooth_m out of range 1..256");
+    if (p->smoother == LQ_SMOOTH_RICHARDSON && !std::isfinite(p->omega)) fail(c, LQ_ERR_ARG, "omega not finite");
+    if (p->smoother == LQ_SMOOTH_GMRES && !(p->smooth_tol >= 0.0)) fail(c, LQ_ERR_ARG, "smooth_tol < 0");
+}
+
+template <typename F>
+lq_status guarded(lq_ctx *c, F &&f)
+{
+    if (!c) return LQ_ERR_ARG;
+    try {
+        int dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != c->device) ck(c, cudaSetDevice(c->device), "cudaSetDevice");
+        f();
+        ck(c, cudaGetLastError(), "kernel launch");
+        return LQ_OK;
+    } catch (const Fail &f) {
+        return f.s;
+    } catch (const std::bad_alloc &) {
+        c->err = "host allocation failed";
+        return LQ_ERR_OOM;
+    }
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+
+extern "C" {
+
+const char *lq_status_string(lq_status s)
+{
+    switch (s) {
+    case LQ_OK: return "LQ_OK";
+    case LQ_ERR_ARG: return "LQ_ERR_ARG";
+    case LQ_ERR_CUDA: return "LQ_ERR_CUDA";
+    case LQ_ERR_OOM: return "LQ_ERR_OOM";
+    case LQ_ERR_NOT_CONVERGED: return "LQ_ERR_NOT_CONVERGED";
+    case LQ_ERR_BREAKDOWN: return "LQ_ERR_BREAKDOWN";
+    case LQ_ERR_NAN: return "LQ_ERR_NAN";
+    case LQ_ERR_STATE: return "LQ_ERR_STATE";
+    }
+    return "LQ_ERR_UNKNOWN";
+}
+
+const char *lq_last_error(lq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
+{
+    if (!out || !lat) return LQ_ERR_ARG;
+    *out = nullptr;
+    for (int mu = 0; mu < 4; mu++)
+        if (lat->L[mu] < 2 || lat->L[mu] % 2) return LQ_ERR_ARG;
+    if (lat->t_bc != 1 && lat->t_bc != -1) return LQ_ERR_ARG;
+    if (!std::isfinite(lat->m0) || !std::isfinite(lat->csw)) return LQ_ERR_ARG;
+    const long long V = (long long)lat->L[0] * lat->L[1] * lat->L[2] * lat->L[3];
+    if (V > (1LL << 40)) return LQ_ERR_ARG;
+    lq_ctx *c = new (std::nothrow) lq_ctx();
+    if (!c) return LQ_ERR_OOM;
+    c->lat = *lat;
+    for (int mu = 0; mu < 4; mu++) c->g.L[mu] = lat->L[mu];
+    c->g.Lxh = lat->L[0] / 2;
+    c->g.tbc = lat->t_bc;
+    c->g.V = V;
+    c->g.Vh = V / 2;
+    c->g.stride = (c->g.Vh + 63) / 64 * 64;
+    c->st = (cudaStream_t)stream;
+    try {
+        ck(c, cudaGetDevice(&c->device), "cudaGetDevice");
+        c->red.blocks = reduction_blocks(c->g);
+        c->red.maxv = RED_SLOTS;
+        c->red.partial = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS * c->red.blocks);
+        c->red.out = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
+        c->d_coef = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
+        c->dflag = (int *)dev_alloc(c, sizeof(int));
+        ck(c, cudaMallocHost((void **)&c->h_pin, sizeof(double) * 4 * RED_SLOTS), "cudaMallocHost");
+    } catch (const Fail &f) {
+        lq_destroy(c);
+        return f.s;
+    }
+    *out = c;
+    return LQ_OK;
+}
+
+lq_status lq_destroy(lq_ctx *c)
+{
+    if (!c) return LQ_ERR_ARG;
+    cudaStreamSynchronize(c->st);
+    for (void *p : c->owned)
+        if (p) cudaFree(p);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    delete c;
+    return LQ_OK;
+}
+
+lq_status lq_set_gauge(lq_ctx *c, const void *U)
+{
+    return guarded(c, [&] {
+        if (!U) fail(c, LQ_ERR_ARG, "U is NULL");
+        Exec e = c->ex();
+        const Geom &g = c->g;
+        if (!c->U64[0]) {
+            for (int p = 0; p < 2; p++) {
+                c->U64[p] = dev_alloc(c, (size_t)4 * 9 * g.stride * 16);
+                c->U32[p] = dev_alloc(c, (size_t)4 * 3 * g.stride * 16);
+                c->C64[p] = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
+                c->C32[p] = dev_alloc(c, (size_t)2 * 9 * g.stride * 16);
+            }
+            c->Ci64 = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
+            c->Ci32 = dev_alloc(c, (size_t)2 * 9 * g.stride * 16);
+        }
+        c->have_gauge = false;
+        import_links(e, U, c->U64, c->U32);
+        clover_build(e, U, c->lat.csw, c->lat.m0, c->C64);
+        ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
+        clover_invert(e, c->C64[1], c->Ci64, c->dflag);
+        clover_to_f32(e, c->C64[0], c->C32[0]);
+        clover_to_f32(e, c->C64[1], c->C32[1]);
+        clover_to_f32(e, c->Ci64, c->Ci32);
+        ck_launch(c, "set_gauge kernels");
+        int flag = 0;
+        ck(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "cudaMemcpyAsync");
+        sync(c);
+        if (flag) fail(c, LQ_ERR_BREAKDOWN, std::to_string(flag) + " clover blocks with a non-positive pivot");
+        c->have_gauge = true;
+    });
+}
+
+lq_status lq_apply(lq_ctx *c, int op, int prec, const void *in, void *out)
+{
+    return guarded(c, [&] {
+        if (!in || !out) fail(c, LQ_ERR_ARG, "NULL field");
+        if (prec != LQ_F64 && prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad precision");
+        need_gauge(c);
+        Exec e = c->ex();
+        void *a = field(c, prec, "apply:a"), *b = field(c, prec, "apply:b");
+        void *d = field(c, prec, "apply:d"), *f = field(c, prec, "apply:f");
+        switch (op) {
+        case LQ_OP_FULL:
+            import_full(e, prec, in, a, b);
+            op_full(c, prec, a, b, d, f);
+            export_full(e, prec, d, f, out);
+            break;
+        case LQ_OP_SCHUR:
+            import_half(e, prec, in, a);
+            op_schur(c, prec, a, d, b);
+            export_half(e, prec, d, out);
+            break;
+        case LQ_OP_SCHUR_DAG:
+            import_half(e, prec, in, a);
+            gamma5(e, prec, a, a);
+            op_schur(c, prec, a, d, b);
+            gamma5(e, prec, d, d);
+            export_half(e, prec, d, out);
+            break;
+        case LQ_OP_EE:
+            import_half(e, prec, in, a);
+            clover_mul(e, prec, Cp(c, prec, 0), a, d);
+            export_half(e, prec, d, out);
+            break;
+        case LQ_OP_OO_INV:
+            import_half(e, prec, in, a);
+            clover_mul(e, prec, Cip(c, prec), a, d);
+            export_half(e, prec, d, out);
+            break;
+        default:
+            fail(c, LQ_ERR_ARG, "bad op");
+        }
+    });
+}
+
+lq_status lq_prepare(lq_ctx *c, const void *b, void *bhat_e)
+{
+    return guarded(c, [&] {
+        if (!b || !bhat_e) fail(c, LQ_ERR_ARG, "NULL field");
+        need_gauge(c);
+        Exec e = c->ex();
+        void *be = field(c, P64, "prep:be"), *bo = field(c, P64, "prep:bo");
+        void *t = field(c, P64, "prep:t"), *o = field(c, P64, "prep:o");
+        import_full(e, P64, b, be, bo);
+        op_prepare(c, P64, be, bo, o, t);
+        export_half(e, P64, o, bhat_e);
+    });
+}
+
+lq_status lq_reconstruct(lq_ctx *c, const void *b, const void *x_e, void *x)
+{
+    return guarded(c, [&] {
+        if (!b || !x_e || !x) fail(c, LQ_ERR_ARG, "NULL field");
+        need_gauge(c);
+        Exec e = c->ex();
+        void *be = field(c, P64, "prep:be"), *bo = field(c, P64, "prep:bo");
+        void *xe = field(c, P64, "prep:t"), *xo = field(c, P64, "prep:o");
+        import_full(e, P64, b, be, bo);
+        import_half(e, P64, x_e, xe);
+        op_reconstruct(c, P64, bo, xe, xo);
+        export_full(e, P64, xe, xo, x);
+    });
+}
+
+lq_status lq_estimate_norm(lq_ctx *c, int iters, const void *v0, double *out)
+{
+    return guarded(c, [&] {
+        if (!v0 || !out || iters < 1) fail(c, LQ_ERR_ARG, "bad argument");
+        need_gauge(c);
+        Exec e = c->ex();
+        void *v = field(c, P64, "pow:v"), *w = field(c, P64, "pow:w");
+        void *u = field(c, P64, "pow:u"), *t = field(c, P64, "pow:t");
+        import_half(e, P64, v0, v);
+        double n0 = norm2_of(c, P64, v);
+        if (!(n0 > 0.0) || !std::isfinite(n0)) fail(c, LQ_ERR_ARG, "v0 is zero or not finite");
+        axpby(e, P64, 0.0, 0.0, v, 1.0 / std::sqrt(n0), 0.0, v);
+        double lam = 0.0;
+        for (int i = 0; i < iters; i++) {
+            op_schur(c, P64, v, u, t);             // u = D_S v
+            gamma5(e, P64, u, u);
+            op_schur(c, P64, u, w, t);             // w = D_S^+ D_S v = g5 D_S g5 D_S v
+            gamma5(e, P64, w, w);
+            lam = std::sqrt(norm2_of(c, P64, w));
+            if (!std::isfinite(lam) || lam == 0.0) fail(c, LQ_ERR_NAN, "power iteration produced 0/NaN");
+            axpby(e, P64, 1.0 / lam, 0.0, w, 0.0, 0.0, v);
+        }
+        *out = std::sqrt(lam);
+    });
+}
+
+lq_status lq_norm2(lq_ctx *c, const void *v, long long n_sites, double *out)
+{
+    return guarded(c, [&] {
+        if (!v || !out || n_sites < 0) fail(c, LQ_ERR_ARG, "bad argument");
+        Exec e = c->ex();
+        nat_norm2(e, v, n_sites, c->red, 0);
+        reduce_finish(e, c->red, 0, 1);
+        ck_launch(c, "norm2");
+        *out = fetch(c, 0, 1)[0];
+    });
+}
+
+lq_status lq_smooth(lq_ctx *c, const lq_solver_params *p, const void *r, void *eo)
+{
+    return guarded(c, [&] {
+        if (!r || !eo) fail(c, LQ_ERR_ARG, "NULL field");
+        check_params(c, p, false);
+        need_gauge(c);
+        Exec e = c->ex();
+        const int q = p->inner_prec;
+        void *re = field(c, P64, "sm:re"), *ro = field(c, P64, "sm:ro");
+        void *rh = field(c, P64, "sm:rh"), *t = field(c, P64, "sm:t");
+        void *ee = field(c, P64, "sm:ee"), *eodd = field(c, P64, "sm:eo");
+        import_full(e, P64, r, re, ro);
+        op_prepare(c, P64, re, ro, rh, t);
+        if (q == P64) {
+            smoother_schur(c, p, P64, rh, ee);
+        } else {
+            void *rq = field(c, q, "sm:rq"), *eq = field(c, q, "sm:eq");
+            convert(e, P64, rh, q, rq);
+            smoother_schur(c, p, q, rq, eq);
+            convert(e, q, eq, P64, ee);
+        }
+        op_reconstruct(c, P64, ro, ee, eodd);
+        export_full(e, P64, ee, eodd, eo);
+    });
+}
+
+lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lq_stats *stats)
+{
+    bool not_conv = false;
+    auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = c ? c->ctr.launches : 0;
+    const double b0 = c ? c->ctr.bytes : 0.0;
+    lq_stats st{};
+    lq_status s = guarded(c, [&] {
+        if (!b || !x) fail(c, LQ_ERR_ARG, "NULL field");
+        check_params(c, p, true);
+        need_gauge(c);
+        Exec e = c->ex();
+        void *be = field(c, P64, "sol:be"), *bo = field(c, P64, "sol:bo");
+        void *xe = field(c, P64, "sol:xe"), *xo = field(c, P64, "sol:xo");
+        void *bh = field(c, P64, "sol:bh"), *t = field(c, P64, "sol:t");
+        import_full(e, P64, b, be, bo);
+        import_full(e, P64, x, xe, xo);
+        op_prepare(c, P64, be, bo, bh, t);
+        KResult R;
+        long long inner = 0;
+        if (p->solver == LQ_SOLVER_GMRES) {
+            if (p->prec == LQ_F64) {
+                R = gmres(c, P64, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV");
+            } else {
+                void *bq = field(c, P32, "sol:bq"), *xq = field(c, P32, "sol:xq");
+                convert(e, P64, bh, P32, bq);
+                convert(e, P64, xe, P32, xq);
+                R = gmres(c, P32, bq, xq, p->restart, p->max_restarts, p->tol, false, "outerV");
+                convert(e, P32, xq, P64, xe);
+            }
+        } else {
+            R = fgmres(c, p, bh, xe, &inner);
+        }
+        op_reconstruct(c, P64, bo, xe, xo);
+        export_full(e, P64, xe, xo, x);
+        // true residual on the full lattice, FP64
+        void *ye = field(c, P64, "sol:ye"), *yo = field(c, P64, "sol:yo");
+        op_full(c, P64, xe, xo, ye, yo);
+        axpby(e, P64, 1.0, 0.0, be, -1.0, 0.0, ye);
+        axpby(e, P64, 1.0, 0.0, bo, -1.0, 0.0, yo);
+        norm2(e, P64, ye, c->red, 0);
+        norm2(e, P64, yo, c->red, 1);
+        norm2(e, P64, be, c->red, 2);
+        norm2(e, P64, bo, c->red, 3);
+        reduce_finish(e, c->red, 0, 4);
+        ck_launch(c, "true residual");
+        const double *hv = fetch(c, 0, 4);
+        const double bn = hv[4] + hv[6];
+        st.rel_resid_true = bn > 0 ? std::sqrt((hv[0] + hv[2]) / bn) : 0.0;
+        st.cycles = R.cycles;
+        st.iters = R.iters;
+        st.inner_iters = inner;
+        st.rel_resid = R.relres;
+        if (!std::isfinite(st.rel_resid_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in the true residual");
+        not_conv = !R.converged;
+    });
+    if (c) {
+        st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        st.launches = c->ctr.launches - l0;
+        st.bytes = c->ctr.bytes - b0;
+    }
+    if (stats) *stats = st;
+    if (s == LQ_OK && not_conv) {
+        c->err = "tolerance not reached within max_restarts";
+        return LQ_ERR_NOT_CONVERGED;
+    }
+    return s;
+}
+
+lq_status lq_export_clover(lq_ctx *c, int which, void *out)
+{
+    return guarded(c, [&] {
+        if (!out || (which != 0 && which != 1)) fail(c, LQ_ERR_ARG, "bad argument");
+        need_gauge(c);
+        Exec e = c->ex();
+        if (which == 0) clover_export(e, c->C64[0], c->C64[1], out);
+        else clover_export(e, nullptr, c->Ci64, out);
+    });
+}
+
+lq_status lq_counters(lq_ctx *c, long long *launches, double *bytes)
+{
+    if (!c) return LQ_ERR_ARG;
+    if (launches) *launches = c->ctr.launches;
+    if (bytes) *bytes = c->ctr.bytes;
+    return LQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// The fused hopping kernels of the odd-even Wilson-clover operator.
+//
+// One thread per output site of one parity.  For each of the eight
+// directions the neighbour spinor is spin-projected onto a half spinor with
+// (1 -+ g_mu), multiplied by the link (U_mu(x) forward, U_mu(x-mu)^+ backward)
+// and reconstructed into the 12-component accumulator; the epilogue then
+// applies the site-diagonal clover block (C or C^{-1}) and whatever BLAS-1
+// step the mode fuses.  Together the two launches
+//   K1: t_o = D_oo^{-1} D_oe x_e      (HOP_K1 on odd sites)
+//   K2: y_e = D_ee x_e - D_eo t_o     (HOP_K2 on even sites)
+// apply the Schur complement D_S of Eq. 3; HOP_RICH fuses the Richardson
+// update x_e += omega (b_e - D_S x_e) of Algorithm 4 into K2.
+//
+// Projection identities used (chiral basis, upper = spins 0,1):
+//   (1 - s g_k) psi = (h, s(-i s_k) h)  with h = psi_u + s i s_k psi_l   (k = 1,2,3)
+//   (1 - s g_4) psi = (h, -s h)         with h = psi_u - s psi_l
+// where s = +1 for the forward and -1 for the backward hop.
+#include "lq_kernels.h"
+
+namespace lq {
+
+#ifndef LQ_HOP_THREADS
+#define LQ_HOP_THREADS 128
+#endif
+
+// half spinor h[hs*3 + a] from the full spinor p[s*3 + a]; SIGN = -1 projects
+// with (1 - g_mu) (forward hop), SIGN = +1 with (1 + g_mu) (backward hop)
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const cx<R> p0 = p[a], p1 = p[3 + a], p2 = p[6 + a], p3 = p[9 + a];
+        if (MU == 0) {
+            h[a] = SIGN < 0 ? p0 + ti(p3) : p0 - ti(p3);
+            h[3 + a] = SIGN < 0 ? p1 + ti(p2) : p1 - ti(p2);
+        } else if (MU == 1) {
+            h[a] = SIGN < 0 ? p0 + p3 : p0 - p3;
+            h[3 + a] = SIGN < 0 ? p1 - p2 : p1 + p2;
+        } else if (MU == 2) {
+            h[a] = SIGN < 0 ? p0 + ti(p2) : p0 - ti(p2);
+            h[3 + a] = SIGN < 0 ? p1 - ti(p3) : p1 + ti(p3);
+        } else {
+            h[a] = SIGN < 0 ? p0 - p2 : p0 + p2;
+            h[3 + a] = SIGN < 0 ? p1 - p3 : p1 + p3;
+        }
+    }
+}
+
+// acc += the full spinor reconstructed from the transported half spinor u
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void reconstruct(cx<R> acc[12], const cx<R> u[6])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const cx<R> u0 = u[a], u1 = u[3 + a];
+        acc[a] = acc[a] + u0;
+        acc[3 + a] = acc[3 + a] + u1;
+        if (MU == 0) {
+            acc[6 + a] = SIGN < 0 ? acc[6 + a] + tmi(u1) : acc[6 + a] + ti(u1);
+            acc[9 + a] = SIGN < 0 ? acc[9 + a] + tmi(u0) : acc[9 + a] + ti(u0);
+        } else if (MU == 1) {
+            acc[6 + a] = SIGN < 0 ? acc[6 + a] - u1 : acc[6 + a] + u1;
+            acc[9 + a] = SIGN < 0 ? acc[9 + a] + u0 : acc[9 + a] - u0;
+        } else if (MU == 2) {
+            acc[6 + a] = SIGN < 0 ? acc[6 + a] + tmi(u0) : acc[6 + a] + ti(u0);
+            acc[9 + a] = SIGN < 0 ? acc[9 + a] + ti(u1) : acc[9 + a] + tmi(u1);
+        } else {
+            acc[6 + a] = SIGN < 0 ? acc[6 + a] - u0 : acc[6 + a] + u0;
+            acc[9 + a] = SIGN < 0 ? acc[9 + a] - u1 : acc[9 + a] + u1;
+        }
+    }
+}
+
+// one hop: acc += (1 -+ g_mu) W psi(nb), W = U_mu(x) (SIGN -1) or U_mu(x-mu)^+ (SIGN +1);
+// `bsign` is the fermion boundary factor of this hop
+template <int MU, int SIGN, typename R, typename V>
+__device__ __forceinline__ void hop_dir(cx<R> acc[12], const V *__restrict__ psi, const V *__restrict__ U,
+                                        long long link_site, long long nb, long long stride, R bsign)
+{
+    cx<R> p[12];
+    load_spinor(psi, stride, nb, p);
+    cx<R> m[9];
+    load_link(U, stride, MU, link_site, m);
+    cx<R> h[6];
+    project<MU, SIGN>(p, h);
+    cx<R> u[6];
+#pragma unroll
+    for (int hs = 0; hs < 2; hs++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cx<R> t;
+            if (SIGN < 0) {
+                t = cmul(m[a * 3 + 0], h[hs * 3 + 0]);
+                t = cfma(m[a * 3 + 1], h[hs * 3 + 1], t);
+                t = cfma(m[a * 3 + 2], h[hs * 3 + 2], t);
+            } else {
+                t = cmulc(m[0 * 3 + a], h[hs * 3 + 0]);
+                t = cfmac(m[1 * 3 + a], h[hs * 3 + 1], t);
+                t = cfmac(m[2 * 3 + a], h[hs * 3 + 2], t);
+            }
+            u[hs * 3 + a] = bsign * t;
+        }
+    reconstruct<MU, SIGN>(acc, u);
+}
+
+template <typename R>
+struct HopArgs {
+    typedef typename St<R>::vec V;
+    const V *in;
+    const V *in2;
+    const V *b;
+    V *out;
+    const V *Uout;   // links of the output parity: forward links U_mu(x)
+    const V *Uin;    // links of the input parity: backward links U_mu(x - mu)
+    const V *clov;
+    R omega;
+    int pout;
+};
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+    const long long st = g.stride;
+    cx<R> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc[i] = {R(0), R(0)};
+    const R one = R(1);
+
+    // x direction: the neighbour changes x, so its cb index is recomputed
+    {
+        const long long base = c.row * g.Lxh;
+        const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
+        const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
+        const long long nf = base + (xp >> 1), nb = base + (xm >> 1);
+        hop_dir<0, -1>(acc, k.in, k.Uout, s, nf, st, one);
+        hop_dir<0, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+    }
+    // y, z, t: x is unchanged, so the cb index moves by a fixed stride
+    {
+        const long long d = g.Lxh;
+        const long long nf = (c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d;
+        const long long nb = (c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d;
+        hop_dir<1, -1>(acc, k.in, k.Uout, s, nf, st, one);
+        hop_dir<1, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+    }
+    {
+        const long long d = (long long)g.Lxh * g.L[1];
+        const long long nf = (c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d;
+        const long long nb = (c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d;
+        hop_dir<2, -1>(acc, k.in, k.Uout, s, nf, st, one);
+        hop_dir<2, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+    }
+    {
+        const long long d = (long long)g.Lxh * g.L[1] * g.L[2];
+        const bool last = (c.t + 1 == g.L[3]), first = (c.t == 0);
+        const long long nf = last ? s - (long long)(g.L[3] - 1) * d : s + d;
+        const long long nb = first ? s + (long long)(g.L[3] - 1) * d : s - d;
+        const R tb = R(g.tbc);
+        hop_dir<3, -1>(acc, k.in, k.Uout, s, nf, st, last ? tb : one);
+        hop_dir<3, +1>(acc, k.in, k.Uin, nb, nb, st, first ? tb : one);
+    }
+
+    cx<R> v[12];
+    if (MODE == HOP_K1) {
+#pragma unroll
+        for (int i = 0; i < 12; i++) acc[i] = R(-0.5) * acc[i];
+        clover_apply<R>(k.clov, st, s, acc, v);
+    } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
+        cx<R> x[12];
+        load_spinor_rw(k.in2, st, s, x);
+        clover_apply<R>(k.clov, st, s, x, v);
+        const R f = MODE == HOP_FULL ? R(-0.5) : R(0.5);
+#pragma unroll
+        for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
+        if (MODE == HOP_RICH) {
+            cx<R> bb[12];
+            load_spinor(k.b, st, s, bb);
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = x[i] + k.omega * (bb[i] - v[i]);
+        }
+    } else {   // HOP_PREP, HOP_RECON
+        cx<R> y[12];
+        load_spinor_rw(k.in2, st, s, y);
+#pragma unroll
+        for (int i = 0; i < 12; i++) y[i] = y[i] + R(0.5) * acc[i];
+        if (MODE == HOP_RECON) {
+            clover_apply<R>(k.clov, st, s, y, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = y[i];
+        }
+    }
+    store_spinor(k.out, st, s, v);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) clover_mul_kernel(Geom g, const typename St<R>::vec *__restrict__ C,
+                                                         const typename St<R>::vec *in, typename St<R>::vec *out)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    cx<R> x[12], y[12];
+    load_spinor_rw(in, g.stride, s, x);
+    clover_apply<R>(C, g.stride, s, x, y);
+    store_spinor(out, g.stride, s, y);
+}
+
+template <typename R, int MODE>
+static void launch_hop(const Exec &e, const HopCall &c)
+{
+    typedef typename St<R>::vec V;
+    HopArgs<R> k;
+    k.in = (const V *)c.in;
+    k.in2 = (const V *)c.in2;
+    k.b = (const V *)c.b;
+    k.out = (V *)c.out;
+    k.Uout = (const V *)c.U[c.pout];
+    k.Uin = (const V *)c.U[1 - c.pout];
+    k.clov = (const V *)c.clov;
+    k.omega = (R)c.omega;
+    k.pout = c.pout;
+    const unsigned blocks = (unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS);
+    hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+}
+
+// algorithmic bytes per output site of one hopping launch
+static double hop_site_bytes(int mode, int prec)
+{
+    const double sp = prec == P64 ? 192.0 : 96.0;          // spinor
+    const double lk = prec == P64 ? 144.0 : 48.0;          // link (18 / 12 reals)
+    const double cl = prec == P64 ? 576.0 : 288.0;         // 72-real clover pair
+    double b = 8 * lk + sp + sp;                            // links, neighbours, output
+    switch (mode) {
+    case HOP_K1: b += cl; break;
+    case HOP_K2: case HOP_FULL: b += sp + cl; break;
+    case HOP_RICH: b += 2 * sp + cl; break;
+    case HOP_PREP: b += sp; break;
+    case HOP_RECON: b += sp + cl; break;
+    }
+    return b;
+}
+
+void hop(const Exec &e, const HopCall &c)
+{
+#define LQ_CASE(M)                                                              \
+    case M:                                                                     \
+        if (c.prec == P64) launch_hop<double, M>(e, c);                         \
+        else launch_hop<float, M>(e, c);                                        \
+        break;
+    switch (c.mode) {
+        LQ_CASE(HOP_K1)
+        LQ_CASE(HOP_K2)
+        LQ_CASE(HOP_RICH)
+        LQ_CASE(HOP_FULL)
+        LQ_CASE(HOP_PREP)
+        LQ_CASE(HOP_RECON)
+    }
+#undef LQ_CASE
+    e.ctr->launches++;
+    e.ctr->bytes += (double)e.g.Vh * hop_site_bytes(c.mode, c.prec);
+}
+
+void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void *out)
+{
+    const unsigned blocks = (unsigned)((e.g.Vh + 255) / 256);
+    if (prec == P64)
+        clover_mul_kernel<double><<<blocks, 256, 0, e.st>>>(e.g, (const double2 *)clov, (const double2 *)in,
+                                                           (double2 *)out);
+    else
+        clover_mul_kernel<float><<<blocks, 256, 0, e.st>>>(e.g, (const float4 *)clov, (const float4 *)in,
+                                                          (float4 *)out);
+    e.ctr->launches++;
+    e.ctr->bytes += (double)e.g.Vh * (prec == P64 ? 192.0 * 2 + 576.0 : 96.0 * 2 + 288.0);
+}
+
+}  // namespace lq

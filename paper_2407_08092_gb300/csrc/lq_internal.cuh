@@ -1,0 +1,290 @@
+// Internal definitions of the GB300 odd-even Wilson-clover library.
+//
+// Internal layout (never visible through the C ABI)
+// -------------------------------------------------
+// Sites of one parity are numbered by the checkerboard index cb = lex/2
+// (Lx even), so a half spinor in natural order is already in cb order.  Every
+// per-site quantity is stored structure-of-arrays over cb with a padded
+// stride (a multiple of 64 sites), in 16-byte vectors so that a warp reads
+// 512 contiguous bytes per component:
+//
+//   spinor   FP64: [12][stride] double2        (component = spin*3 + colour)
+//            FP32: [ 6][stride] float4         (two components per float4)
+//   links    FP64: [4 mu][9][stride] double2   (full 3x3, row-major)
+//            FP32: [4 mu][3][stride] float4    (rows 0 and 1; row 2 = conj(r0 x r1))
+//   clover   [2 blocks][36 reals][stride] as 18 double2 (FP64) or 9 float4 (FP32):
+//            the 6x6 Hermitian block packed as 6 real diagonal entries, then the
+//            15 strictly-lower complex entries (1,0),(2,0),(2,1),(3,0),...,(5,4).
+//
+// Links, clover and spinors exist once per parity; the link array of parity p
+// holds U_mu(x) for the sites x of parity p.  The fermion time boundary sign is
+// applied inside the hopping kernels (not folded into the links), so the same
+// link copies serve the clover term and both precisions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lq {
+
+struct Geom {
+    int L[4];
+    int Lxh;          // Lx / 2
+    int tbc;          // +1 / -1
+    long long V;      // sites
+    long long Vh;     // sites per parity
+    long long stride; // padded Vh
+};
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <typename R>
+struct cx {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+// a * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b)
+{
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b)
+{
+    return {fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re)};
+}
+// acc + a * b
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc)
+{
+    return {fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+}
+// acc + conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cfmac(cx<R> a, cx<R> b, cx<R> acc)
+{
+    return {fma(a.re, b.re, fma(a.im, b.im, acc.re)), fma(a.re, b.im, fma(-a.im, b.re, acc.im))};
+}
+// i * a, -i * a
+template <typename R>
+__device__ __forceinline__ cx<R> ti(cx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cx<R> tmi(cx<R> a) { return {a.im, -a.re}; }
+template <typename R>
+__device__ __forceinline__ cx<R> cconj(cx<R> a) { return {a.re, -a.im}; }
+
+// ---------------------------------------------------------------------------
+// storage traits: 16-byte vectors per precision
+// ---------------------------------------------------------------------------
+template <typename R>
+struct St;
+
+template <>
+struct St<double> {
+    typedef double2 vec;               // one complex per vector
+    static constexpr int SPINOR_VECS = 12;
+    static constexpr int CLOVER_VECS = 18;  // per 6x6 block
+    static constexpr int LINK_VECS = 9;     // 18-real links
+};
+
+template <>
+struct St<float> {
+    typedef float4 vec;                // two complexes per vector
+    static constexpr int SPINOR_VECS = 6;
+    static constexpr int CLOVER_VECS = 9;
+    static constexpr int LINK_VECS = 3;     // 12-real compressed links
+};
+
+template <typename R>
+__host__ __device__ constexpr long long spinor_elems(long long stride)
+{
+    return (long long)St<R>::SPINOR_VECS * stride;   // in vectors
+}
+
+// read-only cached vector loads
+__device__ __forceinline__ double2 ldg(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldg(const float4 *p) { return __ldg(p); }
+
+__device__ __forceinline__ void load_spinor(const double2 *__restrict__ p, long long stride,
+                                            long long s, cx<double> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        double2 t = ldg(p + c * stride + s);
+        v[c] = {t.x, t.y};
+    }
+}
+__device__ __forceinline__ void load_spinor(const float4 *__restrict__ p, long long stride,
+                                            long long s, cx<float> v[12])
+{
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        float4 t = ldg(p + k * stride + s);
+        v[2 * k] = {t.x, t.y};
+        v[2 * k + 1] = {t.z, t.w};
+    }
+}
+// plain (coherent) loads, for vectors the same kernel also writes
+__device__ __forceinline__ void load_spinor_rw(const double2 *p, long long stride, long long s,
+                                               cx<double> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        double2 t = p[c * stride + s];
+        v[c] = {t.x, t.y};
+    }
+}
+__device__ __forceinline__ void load_spinor_rw(const float4 *p, long long stride, long long s,
+                                               cx<float> v[12])
+{
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        float4 t = p[k * stride + s];
+        v[2 * k] = {t.x, t.y};
+        v[2 * k + 1] = {t.z, t.w};
+    }
+}
+__device__ __forceinline__ void store_spinor(double2 *p, long long stride, long long s,
+                                             const cx<double> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) p[c * stride + s] = make_double2(v[c].re, v[c].im);
+}
+__device__ __forceinline__ void store_spinor(float4 *p, long long stride, long long s,
+                                             const cx<float> v[12])
+{
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        p[k * stride + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+}
+
+// ---------------------------------------------------------------------------
+// links
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_link(const double2 *__restrict__ U, long long stride, int mu,
+                                          long long s, cx<double> m[9])
+{
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        double2 t = ldg(U + (mu * 9 + k) * stride + s);
+        m[k] = {t.x, t.y};
+    }
+}
+__device__ __forceinline__ void load_link(const float4 *__restrict__ U, long long stride, int mu,
+                                          long long s, cx<float> m[9])
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float4 t = ldg(U + (mu * 3 + k) * stride + s);
+        m[2 * k] = {t.x, t.y};
+        m[2 * k + 1] = {t.z, t.w};
+    }
+    // SU(3): third row = conj(row0 x row1)
+    m[6] = cconj(cmul(m[1], m[5]) - cmul(m[2], m[4]));
+    m[7] = cconj(cmul(m[2], m[3]) - cmul(m[0], m[5]));
+    m[8] = cconj(cmul(m[0], m[4]) - cmul(m[1], m[3]));
+}
+
+// ---------------------------------------------------------------------------
+// clover blocks (packed Hermitian 6x6)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_block(const double2 *__restrict__ C, long long stride, int blk,
+                                           long long s, double r[36])
+{
+#pragma unroll
+    for (int k = 0; k < 18; k++) {
+        double2 t = ldg(C + (blk * 18 + k) * stride + s);
+        r[2 * k] = t.x;
+        r[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ void load_block(const float4 *__restrict__ C, long long stride, int blk,
+                                           long long s, float r[36])
+{
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        float4 t = ldg(C + (blk * 9 + k) * stride + s);
+        r[4 * k] = t.x;
+        r[4 * k + 1] = t.y;
+        r[4 * k + 2] = t.z;
+        r[4 * k + 3] = t.w;
+    }
+}
+
+// index of the packed strictly-lower entry (i, j), i > j
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i - 1) / 2 + j; }
+
+// y = A x for a packed Hermitian 6x6 block A
+template <typename R>
+__device__ __forceinline__ void herm6_apply(const R a[36], const cx<R> x[6], cx<R> y[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; i++) y[i] = a[i] * x[i];
+#pragma unroll
+    for (int i = 1; i < 6; i++)
+#pragma unroll
+        for (int j = 0; j < i; j++) {
+            const int k = 6 + 2 * tri(i, j);
+            cx<R> l = {a[k], a[k + 1]};
+            y[i] = cfma(l, x[j], y[i]);    // lower entry
+            y[j] = cfmac(l, x[i], y[j]);   // its conjugate above the diagonal
+        }
+}
+
+// y = C x for a full site (both blocks); x, y are 12-component spinors
+template <typename R, typename V>
+__device__ __forceinline__ void clover_apply(const V *__restrict__ C, long long stride, long long s,
+                                             const cx<R> x[12], cx<R> y[12])
+{
+#pragma unroll
+    for (int blk = 0; blk < 2; blk++) {
+        R a[36];
+        load_block(C, stride, blk, s, a);
+        herm6_apply<R>(a, x + 6 * blk, y + 6 * blk);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// site coordinates from the checkerboard index
+// ---------------------------------------------------------------------------
+struct Coords {
+    int x, y, z, t;
+    long long row;   // y + Ly*(z + Lz*t)
+};
+
+__device__ __forceinline__ Coords cb_coords(const Geom &g, long long s, int parity)
+{
+    Coords c;
+    long long row = s / g.Lxh;
+    int xh = (int)(s - row * g.Lxh);
+    c.row = row;
+    c.y = (int)(row % g.L[1]);
+    long long r2 = row / g.L[1];
+    c.z = (int)(r2 % g.L[2]);
+    c.t = (int)(r2 / g.L[2]);
+    c.x = 2 * xh + ((c.y + c.z + c.t + parity) & 1);
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// launch bookkeeping and errors (host)
+// ---------------------------------------------------------------------------
+struct Counters {
+    long long launches = 0;
+    double bytes = 0.0;
+};
+
+}  // namespace lq

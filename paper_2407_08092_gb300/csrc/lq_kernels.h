@@ -1,0 +1,112 @@
+// Host-side launchers of the library's kernels (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lq_internal.cuh"
+
+namespace lq {
+
+enum Prec { P64 = 0, P32 = 1 };
+
+// Execution context of a launcher: geometry, stream and the counters that
+// record launches and algorithmic bytes.
+struct Exec {
+    Geom g;
+    cudaStream_t st;
+    Counters *ctr;
+};
+
+// Bytes of one internal per-parity spinor field in a precision.
+inline size_t spinor_bytes(const Geom &g, int prec)
+{
+    return (size_t)24 * g.stride * (prec == P64 ? 8 : 4);
+}
+
+// ---- layout (layout.cu) ----------------------------------------------------
+// natural complex-double gauge field -> per-parity internal link copies
+void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2]);
+// natural half spinor [Vh][12] c128 <-> internal field of one parity
+void import_half(const Exec &e, int prec, const void *nat, void *f);
+void export_half(const Exec &e, int prec, const void *f, void *nat);
+// natural full spinor [V][12] c128 <-> internal even and odd fields
+void import_full(const Exec &e, int prec, const void *nat, void *fe, void *fo);
+void export_full(const Exec &e, int prec, const void *fe, const void *fo, void *nat);
+// precision conversion between internal fields
+void convert(const Exec &e, int from, const void *in, int to, void *out);
+// out = g5 in (negates spins 2 and 3); in == out allowed
+void gamma5(const Exec &e, int prec, const void *in, void *out);
+
+// ---- clover (clover.cu) ----------------------------------------------------
+// C(x) of every site from the natural gauge field, FP64 packed blocks per parity
+void clover_build(const Exec &e, const void *U_nat, double csw, double m0, void *C64[2]);
+// packed inverse of the blocks of one parity by LDL^+; *flag += failures
+void clover_invert(const Exec &e, const void *C64, void *Cinv64, int *flag);
+// FP64 -> FP32 copy of one parity's packed blocks
+void clover_to_f32(const Exec &e, const void *C64, void *C32);
+// natural export: out[V][2][6][6] c128 from packed blocks (null parity pointer -> zeros)
+void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
+
+// ---- hopping term (dslash.cu) ----------------------------------------------
+// Modes of the fused hopping kernel; acc = sum of the eight hops into x (the
+// hopping term H of the operator) read from the opposite-parity field `in`.
+enum HopMode {
+    HOP_K1 = 0,     // out = Cinv (-1/2 acc)               t_o = D_oo^{-1} D_oe x_e
+    HOP_K2 = 1,     // out = C in2 + 1/2 acc               y_e = D_ee x_e - D_eo t_o
+    HOP_RICH = 2,   // out = in2 + w (b - (C in2 + 1/2 acc))   Richardson sweep on D_S
+    HOP_FULL = 3,   // out = C in2 - 1/2 acc               D on one parity
+    HOP_PREP = 4,   // out = in2 + 1/2 acc                 b_e - D_eo t_o
+    HOP_RECON = 5   // out = Cinv (in2 + 1/2 acc)          D_oo^{-1} (b_o - D_oe x_e)
+};
+struct HopCall {
+    int mode;
+    int prec;
+    int pout;              // parity of the output sites
+    const void *in;        // opposite-parity field (the hops' source)
+    const void *in2;       // same-parity field (mode dependent)
+    const void *b;         // HOP_RICH right-hand side
+    void *out;
+    const void *U[2];      // link copies of both parities (this precision)
+    const void *clov;      // C or C^{-1} of the output parity (this precision)
+    double omega;          // HOP_RICH weight
+};
+void hop(const Exec &e, const HopCall &c);
+// out = C in (site-diagonal apply of packed blocks of one parity)
+void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void *out);
+
+// ---- BLAS-1 and reductions (blas.cu) ----------------------------------------
+// All vectors are internal fields of one parity (or n_vec of them spaced by
+// spinor_bytes apart).  Complex scalars are (re, im) pairs.
+void zero(const Exec &e, int prec, void *x);
+void copy(const Exec &e, int prec, const void *x, void *y);
+// y = a x + b y  (complex a, b; host scalars)
+void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi,
+           void *y);
+// Reduction scratch: per-block partials and the finished values, in device
+// memory owned by the context.  Slot i holds a complex value at [2i, 2i+1].
+struct RedScratch {
+    double *partial;   // [blocks][2 * maxv]
+    double *out;       // [2 * maxv]
+    int blocks;
+    int maxv;
+};
+// y = y - sum_j c_j v_j (sign = -1) or y + sum_j c_j v_j (sign = +1), c in DEVICE
+// memory (complex doubles), v_j = V + j * spinor_bytes; with r non-null also the
+// partials of ||y_new||^2 into slot `slot`
+void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_dev, int sign,
+                void *y, const RedScratch *r, int slot);
+// partials of (v_j, w) = sum conj(v_j) w for j < nv into slots slot0 + j
+void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, const RedScratch &r,
+               int slot0);
+// ||w||^2 into slot `slot` (real part)
+void norm2(const Exec &e, int prec, const void *w, const RedScratch &r, int slot);
+// sum the per-block partials of slots [first, first + count) into r.out
+void reduce_finish(const Exec &e, const RedScratch &r, int first, int count);
+// y = x * (1 / sqrt(r.out[2*slot])) with the norm read on the device
+void scale_by_inv_norm(const Exec &e, int prec, const void *x, const RedScratch &r, int slot,
+                       void *y);
+// norm of a natural c128 field of n sites (used by lq_norm2)
+void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch &r, int slot);
+int reduction_blocks(const Geom &g);
+
+}  // namespace lq

@@ -1,0 +1,193 @@
+"""Python binding of the C ABI in ``include/lqdd.h`` (argument marshalling only).
+
+Every function has the name of its C entry point and forwards to it through
+ctypes; all arithmetic runs in the CUDA library ``liblqdd.so``.  Field
+arguments are CUDA tensors (complex128, contiguous) or raw device pointers.
+There is no fallback: if the library is missing, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqdd.so")
+
+LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN, LQ_ERR_NAN, LQ_ERR_STATE = range(8)
+LQ_F64, LQ_F32 = 0, 1
+LQ_OP_FULL, LQ_OP_SCHUR, LQ_OP_SCHUR_DAG, LQ_OP_EE, LQ_OP_OO_INV = range(5)
+LQ_SOLVER_GMRES, LQ_SOLVER_FGMRES = 0, 1
+LQ_SMOOTH_NONE, LQ_SMOOTH_RICHARDSON, LQ_SMOOTH_GMRES = 0, 1, 2
+
+
+class lq_lattice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("t_bc", ctypes.c_int), ("m0", ctypes.c_double),
+                ("csw", ctypes.c_double)]
+
+
+class lq_solver_params(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("prec", ctypes.c_int), ("tol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("smooth_n", ctypes.c_int), ("smooth_m", ctypes.c_int), ("omega", ctypes.c_double),
+                ("smooth_tol", ctypes.c_double), ("inner_prec", ctypes.c_int)]
+
+
+class lq_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("iters", ctypes.c_int), ("inner_iters", ctypes.c_longlong),
+                ("rel_resid", ctypes.c_double), ("rel_resid_true", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2407_08092_gb300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_lib.lq_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(lq_lattice), _P]
+_lib.lq_destroy.argtypes = [_P]
+_lib.lq_set_gauge.argtypes = [_P, _P]
+_lib.lq_apply.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+_lib.lq_prepare.argtypes = [_P, _P, _P]
+_lib.lq_reconstruct.argtypes = [_P, _P, _P, _P]
+_lib.lq_estimate_norm.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.lq_norm2.argtypes = [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
+_lib.lq_smooth.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, _P]
+_lib.lq_solve.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, _P, ctypes.POINTER(lq_stats)]
+_lib.lq_export_clover.argtypes = [_P, ctypes.c_int, _P]
+_lib.lq_counters.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+_lib.lq_last_error.argtypes = [_P]
+_lib.lq_last_error.restype = ctypes.c_char_p
+_lib.lq_status_string.argtypes = [ctypes.c_int]
+_lib.lq_status_string.restype = ctypes.c_char_p
+for _name in ("lq_create", "lq_destroy", "lq_set_gauge", "lq_apply", "lq_prepare", "lq_reconstruct",
+              "lq_estimate_norm", "lq_norm2", "lq_smooth", "lq_solve", "lq_export_clover", "lq_counters"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+def library():
+    """The loaded ctypes library (for callers that need a raw symbol)."""
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    return _lib.lq_status_string(int(s)).decode()
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        import torch
+        if not x.is_cuda:
+            raise ValueError("field must be a CUDA tensor")
+        if x.dtype != torch.complex128:
+            raise ValueError("field must be complex128")
+        if not x.is_contiguous():
+            raise ValueError("field must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _check(ctx, status: int):
+    if status != LQ_OK:
+        msg = _lib.lq_last_error(ctx).decode() if ctx else ""
+        raise LqError(status, msg)
+
+
+def lq_status_string(s: int) -> str:
+    return _status_name(s)
+
+
+def lq_last_error(ctx) -> str:
+    return _lib.lq_last_error(ctx).decode()
+
+
+def lq_create(lat: lq_lattice, stream: int | None = None):
+    ctx = _P()
+    _check(None, _lib.lq_create(ctypes.byref(ctx), ctypes.byref(lat), _P(stream or 0)))
+    return ctx
+
+
+def lq_destroy(ctx) -> None:
+    _check(None, _lib.lq_destroy(ctx))
+
+
+def lq_set_gauge(ctx, U) -> None:
+    _check(ctx, _lib.lq_set_gauge(ctx, _ptr(U)))
+
+
+def lq_apply(ctx, op: int, prec: int, inp, out) -> None:
+    _check(ctx, _lib.lq_apply(ctx, int(op), int(prec), _ptr(inp), _ptr(out)))
+
+
+def lq_prepare(ctx, b, bhat_e) -> None:
+    _check(ctx, _lib.lq_prepare(ctx, _ptr(b), _ptr(bhat_e)))
+
+
+def lq_reconstruct(ctx, b, x_e, x) -> None:
+    _check(ctx, _lib.lq_reconstruct(ctx, _ptr(b), _ptr(x_e), _ptr(x)))
+
+
+def lq_estimate_norm(ctx, iters: int, v0) -> float:
+    out = ctypes.c_double()
+    _check(ctx, _lib.lq_estimate_norm(ctx, int(iters), _ptr(v0), ctypes.byref(out)))
+    return out.value
+
+
+def lq_norm2(ctx, v, n_sites: int) -> float:
+    out = ctypes.c_double()
+    _check(ctx, _lib.lq_norm2(ctx, _ptr(v), int(n_sites), ctypes.byref(out)))
+    return out.value
+
+
+def lq_smooth(ctx, params: lq_solver_params, r, e) -> None:
+    _check(ctx, _lib.lq_smooth(ctx, ctypes.byref(params), _ptr(r), _ptr(e)))
+
+
+def lq_solve(ctx, params: lq_solver_params, b, x):
+    """Returns (status, stats); raises on every status but OK and NOT_CONVERGED."""
+    st = lq_stats()
+    s = _lib.lq_solve(ctx, ctypes.byref(params), _ptr(b), _ptr(x), ctypes.byref(st))
+    if s not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctx, s)
+    return s, st
+
+
+def lq_export_clover(ctx, which: int, out) -> None:
+    _check(ctx, _lib.lq_export_clover(ctx, int(which), _ptr(out)))
+
+
+def lq_counters(ctx):
+    n = ctypes.c_longlong()
+    b = ctypes.c_double()
+    _check(ctx, _lib.lq_counters(ctx, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
+
+
+# ---- small conveniences (no arithmetic) ----------------------------------------------
+
+def make_lattice(L, t_bc: int = -1, m0: float = 0.0, csw: float = 1.0) -> lq_lattice:
+    lat = lq_lattice()
+    for i in range(4):
+        lat.L[i] = int(L[i])
+    lat.t_bc, lat.m0, lat.csw = int(t_bc), float(m0), float(csw)
+    return lat
+
+
+def make_params(solver=LQ_SOLVER_GMRES, prec=LQ_F64, tol=1e-10, restart=30, max_restarts=1000,
+                smoother=LQ_SMOOTH_NONE, smooth_n=0, smooth_m=1, omega=0.0, smooth_tol=0.0,
+                inner_prec=LQ_F64) -> lq_solver_params:
+    return lq_solver_params(solver, prec, tol, restart, max_restarts, smoother, smooth_n, smooth_m,
+                            omega, smooth_tol, inner_prec)
