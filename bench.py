@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the odd-even Wilson-clover hot path on one GB300 (or N replicas).
+
+Workload (the metric's configuration): a 32^3 x 64 lattice, periodic space /
+antiperiodic time, SU(3) links U = exp(i 0.25 sum_k a_k lambda_k) with
+a_k ~ N(0,1) (seed 1001), c_sw = 1.0, m0 = 0.02, Gaussian complex source
+(seed 2001).  One step is one pass of the whole path through the C ABI:
+
+  1. lq_set_gauge      link import, clover build, D_oo^{-1} (LDL)        (a1-a3)
+  2. lq_estimate_norm  10 FP32 power iterations on D_S^+ D_S -> omega     (a8)
+  3. lq_smooth         odd-even Richardson(5, delta = 0.8) smoother M_5 r (a6, a7)
+  4. lq_solve          odd-even FGMRES(10) in FP64, right-preconditioned by
+                       GMRES(16) in FP32 to 1e-5, to a 1e-10 residual     (a4-a6, a9-a11)
+
+value = algorithmic bytes of every library kernel in the timed steps (the
+library counts them per launch) / device time of the steps, in GB/s, summed
+over ranks.  The plain FP64 GMRES(30) solve of the same system is timed once
+beside it for the mixed-vs-FP64 half of the metric.
+
+--impl reference runs the FP64 CPU oracle instead (the test oracle, as it
+stands) on the host cores: each step applies the oracle's D_S (Eq. 3) to a
+bounded sample of the workload (a 16^3 x 32 lattice with the same parameters).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "odd-even Wilson-clover op GB/s vs HBM peak; mixed vs FP64 solve time @1e-10"
+L_WORK = (32, 32, 32, 64)
+EPS, M0, CSW, TBC = 0.25, 0.02, 1.0, -1
+LINK_SEED, SRC_SEED = 1001, 2001
+L_SAMPLE = (16, 16, 16, 32)
+BYTES_DS_F64 = 4416.0   # algorithmic bytes per even site of one FP64 D_S (18-real links)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+_SAMPLE = {}
+
+
+def oracle_ds_sample(seconds: float, min_apps: int = 3):
+    """Time the FP64 oracle's D_S (Eq. 3) on the 16^3 x 32 sample lattice."""
+    import numpy as np
+
+    import oracle
+    from paper_2407_08092_gb300 import synth
+    if "lat" not in _SAMPLE:
+        U = synth.gauge_links(L_SAMPLE, EPS, LINK_SEED)
+        lat = oracle.Lattice(L_SAMPLE, U, m0=M0, csw=CSW, t_bc=TBC)
+        _ = lat.C, lat.Cinv                  # clover and inverse: setup, not timed
+        _SAMPLE["lat"] = lat
+        _SAMPLE["x"] = synth.gaussian_spinor(lat.Vh, SRC_SEED)
+        lat.schur(_SAMPLE["x"])              # warm
+    lat, x = _SAMPLE["lat"], _SAMPLE["x"]
+    n, t0 = 0, time.perf_counter()
+    while n < min_apps or time.perf_counter() - t0 < seconds:
+        x = lat.schur(x)
+        x /= np.sqrt(np.vdot(x, x).real)
+        n += 1
+    dt = time.perf_counter() - t0
+    gbs = n * lat.Vh * BYTES_DS_F64 / dt / 1e9
+    return gbs, n, dt, oracle.threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = max(1.0, min(10.0, 100.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_ds_sample(per_step, 1)
+    vals, apps, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        g, n, dt, cores = oracle_ds_sample(per_step, 1)
+        vals.append(g)
+        apps += n
+        secs += dt
+    value = apps * (L_SAMPLE[0] * L_SAMPLE[1] * L_SAMPLE[2] * L_SAMPLE[3] // 2) * BYTES_DS_F64 / secs / 1e9
+    sample = (f"FP64 oracle D_S (Eq. 3) applied {apps} times on a 16^3x32 lattice with the 32^3x64 "
+              f"workload's parameters (eps 0.25, m0 0.02, csw 1, antiperiodic t); clover precomputed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "odd-even Wilson-clover D_S, FP64 CPU oracle on a bounded sample",
+                       "lattice": list(L_SAMPLE), "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def traffic_per_site(cls_name: str):
+    """DRAM bytes per output site of a kernel class from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2407_08092_gb300", "csrc", "dslash.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for ln in open(path):
+            parts = ln.split()
+            if len(parts) >= 3 and not ln.startswith("#") and parts[0] == cls_name and parts[2] == h:
+                return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2407_08092_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2407_08092_gb300 import lqdd, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    V = int(np.prod(L_WORK))
+    Vh = V // 2
+    U = synth.gauge_links(L_WORK, EPS, LINK_SEED + rank)
+    b = synth.gaussian_spinor(V, SRC_SEED + rank)
+    stream = torch.cuda.current_stream()
+    ctx = lqdd.lq_create(lqdd.make_lattice(L_WORK, TBC, M0, CSW), stream.cuda_stream)
+    dU = torch.from_numpy(U).to(dev)
+    db = torch.from_numpy(b).to(dev)
+    dbe = db[:Vh].contiguous()
+    x = torch.zeros_like(db)
+    e = torch.empty_like(db)
+    mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, tol=1e-10, restart=10, max_restarts=20,
+                             smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16, smooth_tol=1e-5,
+                             inner_prec=lqdd.LQ_F32)
+    info = {}
+
+    def step(Ud, bd, bed, xd, ed):
+        lqdd.lq_set_gauge(ctx, Ud)
+        nrm = lqdd.lq_estimate_norm(ctx, lqdd.LQ_F32, 10, bed)
+        rich = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=0.8 / nrm,
+                                inner_prec=lqdd.LQ_F32)
+        lqdd.lq_smooth(ctx, rich, bd, ed)
+        xd.zero_()
+        status, st = lqdd.lq_solve(ctx, mixed, bd, xd)
+        if status != lqdd.LQ_OK:
+            raise RuntimeError(f"solve: {lqdd.lq_status_string(status)} {st.as_dict()}")
+        info["solve"] = st.as_dict()
+        info["omega"] = 0.8 / nrm
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(dU, db, dbe, x, e)
+    barrier()
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    lqdd.lq_profile(ctx, True)
+    n0, b0 = lqdd.lq_counters(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.nvtx.range_push("timed")
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(dU, db, dbe, x, e)
+        ev[i][1].record(stream)
+    barrier()
+    torch.cuda.nvtx.range_pop()
+    n1, b1 = lqdd.lq_counters(ctx)
+    ms = sum(a.elapsed_time(z) for a, z in ev)
+    prof = {}
+    for c in range(lqdd.LQ_K_COUNT):
+        nl, cms, cb = lqdd.lq_profile_read(ctx, c)
+        if nl or cms:
+            prof[lqdd.lq_kernel_class_name(c)] = {"launches": nl, "ms": round(cms, 4), "bytes": cb}
+    lqdd.lq_profile(ctx, False)
+    clk = clocks.stop()
+    step_bytes = (b1 - b0) / args.steps
+
+    # the plain FP64 GMRES(30) solve of the same system, timed beside the mixed one
+    fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
+    x.zero_()
+    lqdd.lq_solve(ctx, fp64, db, x)            # allocate the FP64 workspace
+    times = {}
+    for name, prm in (("fp64", fp64), ("mixed", mixed)):
+        best = None
+        for _ in range(2):
+            x.zero_()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            status, st = lqdd.lq_solve(ctx, prm, db, x)
+            z.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(z)
+            if best is None or t < best[0]:
+                best = (t, st.as_dict(), lqdd.lq_status_string(status))
+        times[name] = best
+
+    # e2e: host (pinned) inputs and result, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.from_numpy(U).pin_memory()
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        dU2, db2 = torch.empty_like(dU), torch.empty_like(db)
+        ea, ez = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ea.record(stream)
+        for _ in range(args.steps):
+            dU2.copy_(Uh, non_blocking=True)
+            db2.copy_(bh, non_blocking=True)
+            step(dU2, db2, db2[:Vh].contiguous(), x, e)
+            xh.copy_(x, non_blocking=True)
+        ez.record(stream)
+        barrier()
+        e2e_ms = ea.elapsed_time(ez) / args.steps
+        e2e = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
+               "d2h_bytes_per_step": int(xh.numel() * 16), "step_bytes": step_bytes}
+        lqdd.lq_set_gauge(ctx, dU)
+
+    # max over ranks of the timed region, bytes summed over ranks
+    tot_bytes = step_bytes * args.steps
+    if dist:
+        t = torch.tensor([ms, tot_bytes, (e2e or {}).get("ms_per_step", 0.0)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, tot_bytes = float(tmax[0]), float(tsum[1])
+        if e2e:
+            e2e["ms_per_step"] = float(tmax[2])
+    lqdd.lq_destroy(ctx)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    value = tot_bytes / (ms / 1e3) / 1e9
+    pk = peaks()
+    # dominant kernel class by device time
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roofline = None
+    if dom:
+        name, d = dom
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        tps = traffic_per_site(name)
+        per_launch_sites = Vh
+        roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+                    "peak_src": f"{pk['src']} hbm_gbs (STREAM-style copy)",
+                    "traffic": (tps * per_launch_sites) if tps else None,
+                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                    "avg_launch_us": round(1e3 * d["ms"] / d["launches"], 2)}
+    ops = {}
+    for k in ("hop_k1_f32", "hop_k2_f32", "hop_k1_f64", "hop_k2_f64"):
+        if k in prof and prof[k]["ms"] > 0:
+            ops[k] = {"gbs": round(prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9, 1),
+                      "frac": round(prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                      "avg_launch_us": round(1e3 * prof[k]["ms"] / prof[k]["launches"], 2)}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        g, n, dt, cores = oracle_ds_sample(args.cpu_seconds)
+        cpu = {"value": round(g, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle D_S (Eq. 3) x{n} on a 16^3x32 lattice with this workload's parameters "
+                         f"({dt:.1f} s); GB/s by the same algorithmic byte count as the FP64 D_S kernels"}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "32^3x64 odd-even Wilson-clover step: set_gauge + 10 FP32 power iterations + "
+                               "Richardson(5) FP32 smoother + FGMRES(10) FP64 / GMRES(16) FP32 solve to 1e-10",
+                   "lattice": list(L_WORK), "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC,
+                   "l2": "inputs larger than L2 (gauge field 1.2 GB, each spinor field 0.4 GB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": None if e2e is None else {
+            "value": round(e2e["step_bytes"] * world / (e2e["ms_per_step"] / 1e3) / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
+            "ms_per_step": round(e2e["ms_per_step"], 3)},
+        "gpu_launches": int(n1 - n0),
+        "clocks": clk,
+        "op": ops,
+        "solve": {"mixed_ms": round(times["mixed"][0], 2), "fp64_ms": round(times["fp64"][0], 2),
+                  "speedup": round(times["fp64"][0] / times["mixed"][0], 2),
+                  "mixed": times["mixed"][1], "fp64": times["fp64"][1],
+                  "status": {"mixed": times["mixed"][2], "fp64": times["fp64"][2]}},
+        "kernels": prof,
+        "step_bytes": step_bytes,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

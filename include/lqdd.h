@@ -136,11 +136,13 @@ lq_status lq_prepare(lq_ctx *ctx, const void *b, void *bhat_e);
  * (even part = x_e).  b, x: full spinors; x_e: even half spinor.  FP64. */
 lq_status lq_reconstruct(lq_ctx *ctx, const void *b, const void *x_e, void *x);
 
-/* Power iteration on D_S^+ D_S (Sec. 2.4.4): v = v0/||v0||, then `iters` times
+/* Power iteration on D_S^+ D_S (Sec. 2.4.4: lambda_max "computed approximately
+ * with a few iterations of power iteration"): v = v0/||v0||, then `iters` times
  * w = D_S^+ D_S v, lam = ||w||, v = w/lam; *out = sqrt(lam), an estimate of
- * ||D_S||_2 >= |lambda_max(D_S)| from below.  v0: even half spinor (device).
- * FP64.  Synchronises. */
-lq_status lq_estimate_norm(lq_ctx *ctx, int iters, const void *v0, double *out);
+ * ||D_S||_2 >= |lambda_max(D_S)| from below.  D_S^+ = g5 D_S g5.  v0: even half
+ * spinor (device); the iteration runs in precision `prec` (lq_prec).
+ * Synchronises every iteration. */
+lq_status lq_estimate_norm(lq_ctx *ctx, int prec, int iters, const void *v0, double *out);
 
 /* *out = ||v||^2 for a device field of n_sites sites x 12 complex doubles.
  * Deterministic two-stage FP64 reduction.  Synchronises. */
@@ -165,6 +167,35 @@ lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, v
  * complex double [V][2][6][6], natural site order, block 0 = spins {0,1},
  * block 1 = spins {2,3}, index (spin%2)*3 + colour. */
 lq_status lq_export_clover(lq_ctx *ctx, int which, void *out);
+
+/* Kernel classes of the per-class device timing. */
+typedef enum {
+    LQ_K_HOP_K1_F64 = 0, /* K1: t_o = D_oo^{-1} D_oe x_e, FP64 */
+    LQ_K_HOP_K1_F32,     /* K1, FP32 */
+    LQ_K_HOP_K2_F64,     /* K2: y_e = D_ee x_e - D_eo t_o (and its fused Richardson form), FP64 */
+    LQ_K_HOP_K2_F32,     /* K2, FP32 */
+    LQ_K_HOP_OTHER,      /* full-lattice D, prepare, reconstruct, clover apply */
+    LQ_K_CLOVER,         /* clover build, inverse, FP32 copies, export */
+    LQ_K_LAYOUT,         /* natural <-> internal layout, precision conversion, gamma5 */
+    LQ_K_DOT_F64, LQ_K_DOT_F32,    /* multi-dot products */
+    LQ_K_AXPY_F64, LQ_K_AXPY_F32,  /* axpby / multi-axpy */
+    LQ_K_NORM,           /* norms */
+    LQ_K_FINISH,         /* second stage of the deterministic reductions */
+    LQ_K_COPY,           /* device memset / memcpy steps (not kernels) */
+    LQ_K_COUNT
+} lq_kernel_class;
+
+/* Start (on != 0, clearing earlier records) or stop recording a pair of CUDA
+ * events on the context's stream around every launch. */
+lq_status lq_profile(lq_ctx *ctx, int on);
+
+/* Totals of the records of one kernel class since lq_profile(ctx, 1): launches,
+ * summed device time in milliseconds and algorithmic bytes.  Synchronises.
+ * Any output pointer may be NULL. */
+lq_status lq_profile_read(lq_ctx *ctx, int cls, long long *launches, double *ms, double *bytes);
+
+/* A static name for a kernel class ("" when out of range). */
+const char *lq_kernel_class_name(int cls);
 
 /* Counters since the context was created: kernels launched and their
  * algorithmic bytes.  Either pointer may be NULL. */

@@ -52,8 +52,21 @@ struct lq_ctx {
     std::map<std::string, std::pair<void *, size_t>> ws;
     std::vector<void *> owned;
     std::string err;
-    Exec ex() { return Exec{g, st, &ctr}; }
+    Prof prof;
+    Exec ex() { return Exec{g, st, &ctr, &prof}; }
 };
+
+namespace lq {
+cudaEvent_t Prof::get()
+{
+    if (next == pool.size()) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+        pool.push_back(ev);
+    }
+    return pool[next++];
+}
+}  // namespace lq
 
 namespace {
 
@@ -613,6 +626,7 @@ lq_status lq_destroy(lq_ctx *c)
     for (void *p : c->owned)
         if (p) cudaFree(p);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    for (cudaEvent_t ev : c->prof.pool) cudaEventDestroy(ev);
     delete c;
     return LQ_OK;
 }
@@ -722,27 +736,28 @@ lq_status lq_reconstruct(lq_ctx *c, const void *b, const void *x_e, void *x)
     });
 }
 
-lq_status lq_estimate_norm(lq_ctx *c, int iters, const void *v0, double *out)
+lq_status lq_estimate_norm(lq_ctx *c, int prec, int iters, const void *v0, double *out)
 {
     return guarded(c, [&] {
         if (!v0 || !out || iters < 1) fail(c, LQ_ERR_ARG, "bad argument");
+        if (prec != LQ_F64 && prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad precision");
         need_gauge(c);
         Exec e = c->ex();
-        void *v = field(c, P64, "pow:v"), *w = field(c, P64, "pow:w");
-        void *u = field(c, P64, "pow:u"), *t = field(c, P64, "pow:t");
-        import_half(e, P64, v0, v);
-        double n0 = norm2_of(c, P64, v);
+        void *v = field(c, prec, "pow:v"), *w = field(c, prec, "pow:w");
+        void *u = field(c, prec, "pow:u"), *t = field(c, prec, "pow:t");
+        import_half(e, prec, v0, v);
+        double n0 = norm2_of(c, prec, v);
         if (!(n0 > 0.0) || !std::isfinite(n0)) fail(c, LQ_ERR_ARG, "v0 is zero or not finite");
-        axpby(e, P64, 0.0, 0.0, v, 1.0 / std::sqrt(n0), 0.0, v);
+        axpby(e, prec, 0.0, 0.0, v, 1.0 / std::sqrt(n0), 0.0, v);
         double lam = 0.0;
         for (int i = 0; i < iters; i++) {
-            op_schur(c, P64, v, u, t);             // u = D_S v
-            gamma5(e, P64, u, u);
-            op_schur(c, P64, u, w, t);             // w = D_S^+ D_S v = g5 D_S g5 D_S v
-            gamma5(e, P64, w, w);
-            lam = std::sqrt(norm2_of(c, P64, w));
+            op_schur(c, prec, v, u, t);             // u = D_S v
+            gamma5(e, prec, u, u);
+            op_schur(c, prec, u, w, t);             // w = D_S^+ D_S v = g5 D_S g5 D_S v
+            gamma5(e, prec, w, w);
+            lam = std::sqrt(norm2_of(c, prec, w));
             if (!std::isfinite(lam) || lam == 0.0) fail(c, LQ_ERR_NAN, "power iteration produced 0/NaN");
-            axpby(e, P64, 1.0 / lam, 0.0, w, 0.0, 0.0, v);
+            axpby(e, prec, 1.0 / lam, 0.0, w, 0.0, 0.0, v);
         }
         *out = std::sqrt(lam);
     });
@@ -864,6 +879,44 @@ lq_status lq_export_clover(lq_ctx *c, int which, void *out)
         if (which == 0) clover_export(e, c->C64[0], c->C64[1], out);
         else clover_export(e, nullptr, c->Ci64, out);
     });
+}
+
+lq_status lq_profile(lq_ctx *c, int on)
+{
+    if (!c) return LQ_ERR_ARG;
+    c->prof.recs.clear();
+    c->prof.next = 0;
+    c->prof.on = on != 0;
+    return LQ_OK;
+}
+
+lq_status lq_profile_read(lq_ctx *c, int cls, long long *launches, double *ms, double *bytes)
+{
+    return guarded(c, [&] {
+        if (cls < 0 || cls >= K_COUNT) fail(c, LQ_ERR_ARG, "bad kernel class");
+        sync(c);
+        long long n = 0;
+        double t = 0.0, b = 0.0;
+        for (const auto &r : c->prof.recs) {
+            if (r.cls != cls) continue;
+            float dt = 0.0f;
+            ck(c, cudaEventElapsedTime(&dt, r.a, r.b), "cudaEventElapsedTime");
+            n++;
+            t += dt;
+            b += r.bytes;
+        }
+        if (launches) *launches = n;
+        if (ms) *ms = t;
+        if (bytes) *bytes = b;
+    });
+}
+
+const char *lq_kernel_class_name(int cls)
+{
+    static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
+                                         "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
+                                         "norm", "reduce_finish", "copy"};
+    return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 
 lq_status lq_counters(lq_ctx *c, long long *launches, double *bytes)

@@ -255,31 +255,31 @@ static inline double sp_bytes(int prec) { return prec == P64 ? 192.0 : 96.0; }
 
 void zero(const Exec &e, int prec, void *x)
 {
+    Launch L_(e, K_COPY, (double)e.g.Vh * sp_bytes(prec));
     cudaMemsetAsync(x, 0, spinor_bytes(e.g, prec), e.st);
-    e.ctr->bytes += (double)e.g.Vh * sp_bytes(prec);
 }
 
 void copy(const Exec &e, int prec, const void *x, void *y)
 {
+    Launch L_(e, K_COPY, 2.0 * e.g.Vh * sp_bytes(prec));
     cudaMemcpyAsync(y, x, spinor_bytes(e.g, prec), cudaMemcpyDeviceToDevice, e.st);
-    e.ctr->bytes += 2.0 * e.g.Vh * sp_bytes(prec);
 }
 
 void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi, void *y)
 {
+    Launch L_(e, (prec == P64 ? K_AXPY_F64 : K_AXPY_F32), 3.0 * e.g.Vh * sp_bytes(prec));
     if (prec == P64)
         axpby_kernel<double><<<nblk(e.g.Vh), RT, 0, e.st>>>(e.g, ar, ai, (const double2 *)x, br, bi, (double2 *)y);
     else
         axpby_kernel<float><<<nblk(e.g.Vh), RT, 0, e.st>>>(e.g, (float)ar, (float)ai, (const float4 *)x, (float)br,
                                                           (float)bi, (float4 *)y);
-    e.ctr->launches++;
-    e.ctr->bytes += 3.0 * e.g.Vh * sp_bytes(prec);
 }
 
 void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_dev, int sign, void *y,
                 const RedScratch *r, int slot)
 {
     if (nv <= 0 && !r) return;
+    Launch L_(e, (prec == P64 ? K_AXPY_F64 : K_AXPY_F32), (double)e.g.Vh * sp_bytes(prec) * (nv + 2));
     const int blocks = reduction_blocks(e.g);
     const int pitch = r ? 2 * r->maxv : 0;
     double *part = r ? r->partial : nullptr;
@@ -304,13 +304,12 @@ void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_
                                                                      (const double2 *)c_dev, (float)sign,
                                                                      (float4 *)y, part, pitch, slot);
     }
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * sp_bytes(prec) * (nv + 2);
 }
 
 void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, const RedScratch &r, int slot0)
 {
     if (nv <= 0) return;
+    Launch L_(e, (prec == P64 ? K_DOT_F64 : K_DOT_F32), (double)e.g.Vh * sp_bytes(prec) * (nv + (nv + MAXJ - 1) / MAXJ));
     const int pitch = 2 * r.maxv;
     if (prec == P64)
         multi_dot_kernel<double><<<r.blocks, RT, 0, e.st>>>(e.g, (const double2 *)V, 12 * e.g.stride, nv,
@@ -318,45 +317,39 @@ void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, co
     else
         multi_dot_kernel<float><<<r.blocks, RT, 0, e.st>>>(e.g, (const float4 *)V, 6 * e.g.stride, nv,
                                                            (const float4 *)w, r.partial, pitch, slot0);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * sp_bytes(prec) * (nv + (nv + MAXJ - 1) / MAXJ);
 }
 
 void norm2(const Exec &e, int prec, const void *w, const RedScratch &r, int slot)
 {
+    Launch L_(e, K_NORM, (double)e.g.Vh * sp_bytes(prec));
     const int pitch = 2 * r.maxv;
     if (prec == P64)
         norm2_kernel<double><<<r.blocks, RT, 0, e.st>>>(e.g, (const double2 *)w, r.partial, pitch, slot);
     else
         norm2_kernel<float><<<r.blocks, RT, 0, e.st>>>(e.g, (const float4 *)w, r.partial, pitch, slot);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * sp_bytes(prec);
 }
 
 void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch &r, int slot)
 {
+    Launch L_(e, K_NORM, (double)n_sites * 192.0);
     const int pitch = 2 * r.maxv;
     nat_norm2_kernel<<<r.blocks, RT, 0, e.st>>>((const double2 *)v, n_sites * 12, r.partial, pitch, slot);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)n_sites * 192.0;
 }
 
 void reduce_finish(const Exec &e, const RedScratch &r, int first, int count)
 {
     if (count <= 0) return;
+    Launch L_(e, K_FINISH, (double)r.blocks * 2 * count * 8.0);
     reduce_finish_kernel<<<2 * count, RT, 0, e.st>>>(r.partial + 2 * first, r.blocks, 2 * r.maxv, r.out + 2 * first);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)r.blocks * 2 * count * 8.0;
 }
 
 void scale_by_inv_norm(const Exec &e, int prec, const void *x, const RedScratch &r, int slot, void *y)
 {
+    Launch L_(e, (prec == P64 ? K_AXPY_F64 : K_AXPY_F32), 2.0 * e.g.Vh * sp_bytes(prec));
     if (prec == P64)
         scale_kernel<double><<<nblk(e.g.Vh), RT, 0, e.st>>>(e.g, (const double2 *)x, r.out + 2 * slot, (double2 *)y);
     else
         scale_kernel<float><<<nblk(e.g.Vh), RT, 0, e.st>>>(e.g, (const float4 *)x, r.out + 2 * slot, (float4 *)y);
-    e.ctr->launches++;
-    e.ctr->bytes += 2.0 * e.g.Vh * sp_bytes(prec);
 }
 
 }  // namespace lq

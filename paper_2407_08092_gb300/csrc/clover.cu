@@ -316,33 +316,29 @@ static inline unsigned blocks_for(long long n, int threads) { return (unsigned)(
 
 void clover_build(const Exec &e, const void *U_nat, double csw, double m0, void *C64[2])
 {
+    Launch L_(e, K_CLOVER, (double)e.g.V * (4 * 9 * 16 + 72 * 8));
     clover_build_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(
         e.g, (const double2 *)U_nat, csw, m0, (double2 *)C64[0], (double2 *)C64[1]);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.V * (4 * 9 * 16 + 72 * 8);
 }
 
 void clover_invert(const Exec &e, const void *C64, void *Cinv64, int *flag)
 {
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 2 * 72 * 8);
     clover_invert_kernel<<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(e.g, (const double2 *)C64,
                                                                         (double2 *)Cinv64, flag);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * 2 * 72 * 8;
 }
 
 void clover_to_f32(const Exec &e, const void *C64, void *C32)
 {
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 4));
     clover_f32_kernel<<<blocks_for(2 * e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)C64, (float4 *)C32);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * 72 * (8 + 4);
 }
 
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out)
 {
+    Launch L_(e, K_CLOVER, (double)e.g.V * (72 * 8 + 72 * 16));
     clover_export_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(e.g, (const double2 *)Ce,
                                                                   (const double2 *)Co, (double2 *)out);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.V * (72 * 8 + 72 * 16);
 }
 
 }  // namespace lq

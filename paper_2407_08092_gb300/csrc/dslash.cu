@@ -251,6 +251,7 @@ void hop(const Exec &e, const HopCall &c)
         if (c.prec == P64) launch_hop<double, M>(e, c);                         \
         else launch_hop<float, M>(e, c);                                        \
         break;
+    Launch L_(e, (c.mode == HOP_K1 ? (c.prec == P64 ? K_HOP_K1_F64 : K_HOP_K1_F32) : (c.mode == HOP_K2 || c.mode == HOP_RICH) ? (c.prec == P64 ? K_HOP_K2_F64 : K_HOP_K2_F32) : K_HOP_OTHER), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec));
     switch (c.mode) {
         LQ_CASE(HOP_K1)
         LQ_CASE(HOP_K2)
@@ -260,12 +261,11 @@ void hop(const Exec &e, const HopCall &c)
         LQ_CASE(HOP_RECON)
     }
 #undef LQ_CASE
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * hop_site_bytes(c.mode, c.prec);
 }
 
 void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void *out)
 {
+    Launch L_(e, K_HOP_OTHER, (double)e.g.Vh * (prec == P64 ? 192.0 * 2 + 576.0 : 96.0 * 2 + 288.0));
     const unsigned blocks = (unsigned)((e.g.Vh + 255) / 256);
     if (prec == P64)
         clover_mul_kernel<double><<<blocks, 256, 0, e.st>>>(e.g, (const double2 *)clov, (const double2 *)in,
@@ -273,8 +273,6 @@ void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void 
     else
         clover_mul_kernel<float><<<blocks, 256, 0, e.st>>>(e.g, (const float4 *)clov, (const float4 *)in,
                                                           (float4 *)out);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * (prec == P64 ? 192.0 * 2 + 576.0 : 96.0 * 2 + 288.0);
 }
 
 }  // namespace lq

@@ -37,10 +37,9 @@ __global__ void import_links_kernel(Geom g, const double2 *__restrict__ U, doubl
 
 void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2])
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.V * 4 * (144 + 144 + 48));
     import_links_kernel<<<nblk(4 * e.g.V, 256), 256, 0, e.st>>>(
         e.g, (const double2 *)U_nat, (double2 *)U64[0], (double2 *)U64[1], (float4 *)U32[0], (float4 *)U32[1]);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.V * 4 * (144 + 144 + 48);
 }
 
 // ---- spinors ----------------------------------------------------------------
@@ -144,46 +143,42 @@ __global__ void export_full_kernel(Geom g, const typename St<R>::vec *__restrict
 
 void import_half(const Exec &e, int prec, const void *nat, void *f)
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P64 ? 192 : 96)));
     if (prec == P64)
         import_half_kernel<double><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (double2 *)f);
     else
         import_half_kernel<float><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (float4 *)f);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * (192 + (prec == P64 ? 192 : 96));
 }
 
 void export_half(const Exec &e, int prec, const void *f, void *nat)
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P64 ? 192 : 96)));
     if (prec == P64)
         export_half_kernel<double><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)f, (double2 *)nat);
     else
         export_half_kernel<float><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)f, (double2 *)nat);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * (192 + (prec == P64 ? 192 : 96));
 }
 
 void import_full(const Exec &e, int prec, const void *nat, void *fe, void *fo)
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.V * (192 + (prec == P64 ? 192 : 96)));
     if (prec == P64)
         import_full_kernel<double><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (double2 *)fe,
                                                                        (double2 *)fo);
     else
         import_full_kernel<float><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (float4 *)fe,
                                                                       (float4 *)fo);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.V * (192 + (prec == P64 ? 192 : 96));
 }
 
 void export_full(const Exec &e, int prec, const void *fe, const void *fo, void *nat)
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.V * (192 + (prec == P64 ? 192 : 96)));
     if (prec == P64)
         export_full_kernel<double><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)fe,
                                                                        (const double2 *)fo, (double2 *)nat);
     else
         export_full_kernel<float><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const float4 *)fe,
                                                                       (const float4 *)fo, (double2 *)nat);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.V * (192 + (prec == P64 ? 192 : 96));
 }
 
 // ---- conversion and gamma_5 -------------------------------------------------
@@ -215,12 +210,11 @@ void convert(const Exec &e, int from, const void *in, int to, void *out)
         copy(e, from, in, out);
         return;
     }
+    Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + 96));
     if (from == P64)
         d2f_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)in, (float4 *)out);
     else
         f2d_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)in, (double2 *)out);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * (192 + 96);
 }
 
 // gamma_5 = diag(1, 1, -1, -1): negate the components of spins 2 and 3
@@ -250,12 +244,11 @@ __global__ void gamma5_f_kernel(Geom g, const float4 *in, float4 *out)
 
 void gamma5(const Exec &e, int prec, const void *in, void *out)
 {
+    Launch L_(e, K_LAYOUT, (double)e.g.Vh * 2 * (prec == P64 ? 192 : 96));
     if (prec == P64)
         gamma5_d_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)in, (double2 *)out);
     else
         gamma5_f_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)in, (float4 *)out);
-    e.ctr->launches++;
-    e.ctr->bytes += (double)e.g.Vh * 2 * (prec == P64 ? 192 : 96);
 }
 
 }  // namespace lq

@@ -3,18 +3,69 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "lq_internal.cuh"
 
 namespace lq {
 
 enum Prec { P64 = 0, P32 = 1 };
 
-// Execution context of a launcher: geometry, stream and the counters that
-// record launches and algorithmic bytes.
+// Kernel classes for the per-class device timing (mirrors lq_kernel_class of
+// the public header).
+enum KClass {
+    K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
+    K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY, K_COUNT
+};
+
+// Optional CUDA-event timing of every launch (enabled by lq_profile).
+struct Prof {
+    bool on = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<cudaEvent_t> pool;
+    size_t next = 0;
+    std::vector<Rec> recs;
+    cudaEvent_t get();
+};
+
+// Execution context of a launcher: geometry, stream, counters of launches and
+// algorithmic bytes, and the optional profiler.
 struct Exec {
     Geom g;
     cudaStream_t st;
     Counters *ctr;
+    Prof *prof;
+};
+
+// Accounts one launch: records a start event at construction and an end
+// event, the launch count and the algorithmic bytes at destruction.  Kernel
+// launches count toward `launches`; memset/memcpy steps (K_COPY) do not.
+struct Launch {
+    const Exec &e;
+    int cls;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    Launch(const Exec &e_, int cls_, double bytes_) : e(e_), cls(cls_), bytes(bytes_)
+    {
+        if (e.prof && e.prof->on) {
+            a = e.prof->get();
+            cudaEventRecord(a, e.st);
+        }
+    }
+    ~Launch()
+    {
+        if (cls != K_COPY) e.ctr->launches++;
+        e.ctr->bytes += bytes;
+        if (a) {
+            cudaEvent_t b = e.prof->get();
+            cudaEventRecord(b, e.st);
+            e.prof->recs.push_back({cls, a, b, bytes});
+        }
+    }
 };
 
 // Bytes of one internal per-parity spinor field in a precision.

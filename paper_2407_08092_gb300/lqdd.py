@@ -59,18 +59,24 @@ _lib.lq_set_gauge.argtypes = [_P, _P]
 _lib.lq_apply.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
 _lib.lq_prepare.argtypes = [_P, _P, _P]
 _lib.lq_reconstruct.argtypes = [_P, _P, _P, _P]
-_lib.lq_estimate_norm.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.lq_estimate_norm.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
 _lib.lq_norm2.argtypes = [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
 _lib.lq_smooth.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, _P]
 _lib.lq_solve.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, _P, ctypes.POINTER(lq_stats)]
 _lib.lq_export_clover.argtypes = [_P, ctypes.c_int, _P]
 _lib.lq_counters.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+_lib.lq_profile.argtypes = [_P, ctypes.c_int]
+_lib.lq_profile_read.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+_lib.lq_kernel_class_name.argtypes = [ctypes.c_int]
+_lib.lq_kernel_class_name.restype = ctypes.c_char_p
 _lib.lq_last_error.argtypes = [_P]
 _lib.lq_last_error.restype = ctypes.c_char_p
 _lib.lq_status_string.argtypes = [ctypes.c_int]
 _lib.lq_status_string.restype = ctypes.c_char_p
 for _name in ("lq_create", "lq_destroy", "lq_set_gauge", "lq_apply", "lq_prepare", "lq_reconstruct",
-              "lq_estimate_norm", "lq_norm2", "lq_smooth", "lq_solve", "lq_export_clover", "lq_counters"):
+              "lq_estimate_norm", "lq_norm2", "lq_smooth", "lq_solve", "lq_export_clover", "lq_counters",
+              "lq_profile", "lq_profile_read"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -140,9 +146,9 @@ def lq_reconstruct(ctx, b, x_e, x) -> None:
     _check(ctx, _lib.lq_reconstruct(ctx, _ptr(b), _ptr(x_e), _ptr(x)))
 
 
-def lq_estimate_norm(ctx, iters: int, v0) -> float:
+def lq_estimate_norm(ctx, prec: int, iters: int, v0) -> float:
     out = ctypes.c_double()
-    _check(ctx, _lib.lq_estimate_norm(ctx, int(iters), _ptr(v0), ctypes.byref(out)))
+    _check(ctx, _lib.lq_estimate_norm(ctx, int(prec), int(iters), _ptr(v0), ctypes.byref(out)))
     return out.value
 
 
@@ -174,6 +180,26 @@ def lq_counters(ctx):
     b = ctypes.c_double()
     _check(ctx, _lib.lq_counters(ctx, ctypes.byref(n), ctypes.byref(b)))
     return n.value, b.value
+
+
+LQ_K_COUNT = 14
+
+
+def lq_profile(ctx, on: bool) -> None:
+    _check(ctx, _lib.lq_profile(ctx, 1 if on else 0))
+
+
+def lq_profile_read(ctx, cls: int):
+    """(launches, milliseconds, algorithmic bytes) of one kernel class."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(ctx, _lib.lq_profile_read(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+    return n.value, ms.value, b.value
+
+
+def lq_kernel_class_name(cls: int) -> str:
+    return _lib.lq_kernel_class_name(int(cls)).decode()
 
 
 # ---- small conveniences (no arithmetic) ----------------------------------------------

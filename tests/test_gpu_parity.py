@@ -91,7 +91,7 @@ def test_estimate_norm(pair, lqdd):
     lat = pair.lat
     v0 = synth.gaussian_spinor(lat.Vh, 5000 + lat.V)
     for iters in (1, 7):
-        got = lqdd.lq_estimate_norm(pair.ctx, iters, pair.dev(v0))
+        got = lqdd.lq_estimate_norm(pair.ctx, 0, iters, pair.dev(v0))
         ref = oracle.power_norm(lat.schur, lat.schur_dag, v0, iters)
         assert abs(got - ref) <= 1e-12 * ref
 
@@ -140,7 +140,7 @@ def test_solve(pair, lqdd, kind):
     b = synth.gaussian_spinor(lat.V, 8000 + lat.V)
     db = pair.dev(b)
     x = pair.torch.zeros_like(db)
-    norm = lqdd.lq_estimate_norm(pair.ctx, 20, pair.dev(b[:lat.Vh]))
+    norm = lqdd.lq_estimate_norm(pair.ctx, 0, 20, pair.dev(b[:lat.Vh]))
     if kind == "gmres64":
         p = lqdd.make_params(tol=1e-10, restart=30, max_restarts=400)
     elif kind == "fgmres_rich32":
