@@ -201,6 +201,33 @@ const char *lq_kernel_class_name(int cls);
  * algorithmic bytes.  Either pointer may be NULL. */
 lq_status lq_counters(lq_ctx *ctx, long long *launches, double *bytes);
 
+/* Largest field lq_norm2_noalloc accepts, in sites (12 complex doubles each):
+ * 4096 partial sums of 8192 complex values each, divided by 12. */
+#define LQ_NORM2_NOALLOC_MAX_SITES 2796202LL
+
+/* The paper has no counterpart of this call: it serves callers that cannot
+ * allocate device memory (for example code that works inside a fixed memory
+ * budget handed out by another framework, where a cudaMalloc could fail or
+ * synchronise the device at the wrong moment).  It computes the same value as
+ * lq_norm2 -- *out = ||v||^2 for a device field of n_sites sites x 12 complex
+ * doubles -- but needs no context and allocates nothing: its reduction scratch
+ * is a static device array of 4096 doubles (32 KiB) inside the library, which
+ * every GPU that loads the library keeps until the process exits.
+ *   v:      device, n_sites x 12 complex doubles (may be NULL when n_sites == 0)
+ *   out:    device pointer to ONE double, written on `stream`
+ *   stream: cudaStream_t (NULL: the legacy default stream)
+ * The call only enqueues work and does not synchronise.  The first call on a
+ * device looks up the scratch array's device address for that device (with it
+ * current) and caches it; make that first call before any stream capture.
+ * All calls share the one scratch array, which keeps the last call's partial
+ * sums; each call writes every slot it reads, so nothing needs clearing, but
+ * calls whose kernels overlap on the GPU (different streams, or different host
+ * threads on one device) race on it and must be serialised by the caller.
+ * Errors: LQ_ERR_ARG for a NULL pointer, n_sites < 0 or
+ * n_sites > LQ_NORM2_NOALLOC_MAX_SITES (nothing is launched); LQ_ERR_CUDA if
+ * the device, the scratch address or a launch fails. */
+lq_status lq_norm2_noalloc(const void *v, long long n_sites, double *out, void *stream);
+
 /* A static description of the last failure on this context ("" if none). */
 const char *lq_last_error(lq_ctx *ctx);
 

@@ -68,6 +68,8 @@ _lib.lq_counters.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINT
 _lib.lq_profile.argtypes = [_P, ctypes.c_int]
 _lib.lq_profile_read.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+_lib.lq_norm2_noalloc.argtypes = [_P, ctypes.c_longlong, _P, _P]
+_lib.lq_norm2_noalloc.restype = ctypes.c_int
 _lib.lq_kernel_class_name.argtypes = [ctypes.c_int]
 _lib.lq_kernel_class_name.restype = ctypes.c_char_p
 _lib.lq_last_error.argtypes = [_P]
@@ -156,6 +158,26 @@ def lq_norm2(ctx, v, n_sites: int) -> float:
     out = ctypes.c_double()
     _check(ctx, _lib.lq_norm2(ctx, _ptr(v), int(n_sites), ctypes.byref(out)))
     return out.value
+
+
+LQ_NORM2_NOALLOC_MAX_SITES = 2796202
+
+
+def lq_norm2_noalloc(v, n_sites: int, out, stream: int | None = None) -> None:
+    """||v||^2 into the device double `out`, without any device allocation and
+    without a context (for callers that cannot allocate device memory).  `out`
+    is a CUDA float64 tensor of one element or a raw device pointer; the call
+    only enqueues work on `stream`."""
+    if hasattr(out, "data_ptr"):
+        import torch
+        if not out.is_cuda or out.dtype != torch.float64 or out.numel() < 1:
+            raise ValueError("out must be a CUDA float64 tensor with at least one element")
+        out_p = out.data_ptr()
+    else:
+        out_p = int(out)
+    s = _lib.lq_norm2_noalloc(_P(_ptr(v) if int(n_sites) > 0 else 0), int(n_sites), _P(out_p), _P(stream or 0))
+    if s != LQ_OK:
+        raise LqError(s, "lq_norm2_noalloc")
 
 
 def lq_smooth(ctx, params: lq_solver_params, r, e) -> None:
