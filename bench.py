@@ -9,13 +9,14 @@ a_k ~ N(0,1) (seed 1001), c_sw = 1.0, m0 = 0.02, Gaussian complex source
   1. lq_set_gauge      link import, clover build, D_oo^{-1} (LDL)        (a1-a3)
   2. lq_estimate_norm  10 FP32 power iterations on D_S^+ D_S -> omega     (a8)
   3. lq_smooth         odd-even Richardson(5, delta = 0.8) smoother M_5 r (a6, a7)
-  4. lq_solve          odd-even FGMRES(10) in FP64, right-preconditioned by
-                       GMRES(16) in FP32 to 1e-5, to a 1e-10 residual     (a4-a6, a9-a11)
+  4. lq_solve          odd-even FGMRES(10) in df64 (FP64-accurate double-float),
+                       right-preconditioned by GMRES(16) in FP32 to 1e-5, to a
+                       1e-10 residual                                      (a4-a6, a9-a11)
 
 value = algorithmic bytes of every library kernel in the timed steps (the
 library counts them per launch) / device time of the steps, in GB/s, summed
-over ranks.  The plain FP64 GMRES(30) solve of the same system is timed once
-beside it for the mixed-vs-FP64 half of the metric.
+over ranks.  The plain FP64 GMRES(30) solve of the same system (native FP64
+and df64) is timed beside it for the mixed-vs-FP64 half of the metric.
 
 --impl reference runs the FP64 CPU oracle instead (the test oracle, as it
 stands) on the host cores: each step applies the oracle's D_S (Eq. 3) to a
@@ -202,6 +203,39 @@ def traffic_per_site(cls_name: str):
     return None
 
 
+# Kernel classes whose roof is arithmetic, not HBM: native FP64 runs on the
+# FP64 pipe (GB300: 2 FMA/clk/SM -> 152 * 2 * 2 flop * 2.07 GHz = 1.26 TFLOP/s,
+# the nominal 1.25 TFLOP/s), df64 on the FP32 pipe at 15 FP32 instructions per
+# df64 FMA (2prod 2, cross terms 2, 2sum 6, low-part adds 2, fast2sum 3):
+# 152 * 128 lanes * 2.07 GHz / 15 * 2 flop = 5.37 TFLOP/s FP64-equivalent.
+ALU_F64 = {"hop_k1_f64", "hop_k2_f64"}
+ALU_DF64 = {"hop_k1_df64", "hop_k2_df64", "hop_other", "clover"}
+SM_MHZ_MAX = 2070.0
+
+
+def roofline_of(name, d, pk, sites):
+    t = d["ms"] / 1e3
+    base = {"kernel": name, "avg_launch_us": round(1e3 * d["ms"] / d["launches"], 2),
+            "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+            "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+            "gbs": round(d["bytes"] / t / 1e9, 1), "hbm_frac": round(d["bytes"] / t / 1e9 / pk["hbm_gbs"], 4)}
+    if name in ALU_F64 or name in ALU_DF64:
+        peak = (152 * 2 * 2 * SM_MHZ_MAX * 1e6 if name in ALU_F64 else 152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2) / 1e12
+        ach = d["flops"] / t / 1e12
+        base.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 4), "traffic": None,
+                     "peak_src": "derived: " + ("FP64 pipe, 2 FMA/clk/SM" if name in ALU_F64
+                                                else "FP32 pipe, 15 instructions per df64 FMA")
+                                 + f" at {SM_MHZ_MAX:.0f} MHz"})
+    else:
+        ach = d["bytes"] / t / 1e9
+        tps = traffic_per_site(name)
+        base.update({"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(ach / pk["hbm_gbs"], 4), "traffic": (tps * sites) if tps else None,
+                     "peak_src": f"{pk['src']} hbm_gbs (STREAM-style copy)"})
+    return base
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -233,16 +267,16 @@ def run_ours(args):
     dbe = db[:Vh].contiguous()
     x = torch.zeros_like(db)
     e = torch.empty_like(db)
-    mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, tol=1e-10, restart=10, max_restarts=20,
-                             smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16, smooth_tol=1e-5,
-                             inner_prec=lqdd.LQ_F32)
+    mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                             smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
     info = {}
 
     def step(Ud, bd, bed, xd, ed):
         lqdd.lq_set_gauge(ctx, Ud)
         nrm = lqdd.lq_estimate_norm(ctx, lqdd.LQ_F32, 10, bed)
-        rich = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=0.8 / nrm,
-                                inner_prec=lqdd.LQ_F32)
+        rich = lqdd.make_params(prec=lqdd.LQ_DF64, smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5,
+                                omega=0.8 / nrm, inner_prec=lqdd.LQ_F32)
         lqdd.lq_smooth(ctx, rich, bd, ed)
         xd.zero_()
         status, st = lqdd.lq_solve(ctx, mixed, bd, xd)
@@ -277,19 +311,22 @@ def run_ours(args):
     ms = sum(a.elapsed_time(z) for a, z in ev)
     prof = {}
     for c in range(lqdd.LQ_K_COUNT):
-        nl, cms, cb = lqdd.lq_profile_read(ctx, c)
+        nl, cms, cb, cf = lqdd.lq_profile_read(ctx, c)
         if nl or cms:
-            prof[lqdd.lq_kernel_class_name(c)] = {"launches": nl, "ms": round(cms, 4), "bytes": cb}
+            prof[lqdd.lq_kernel_class_name(c)] = {"launches": nl, "ms": round(cms, 4), "bytes": cb, "flops": cf}
     lqdd.lq_profile(ctx, False)
     clk = clocks.stop()
     step_bytes = (b1 - b0) / args.steps
 
     # the plain FP64 GMRES(30) solve of the same system, timed beside the mixed one
     fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
+    df64 = lqdd.make_params(prec=lqdd.LQ_DF64, tol=1e-10, restart=30, max_restarts=200)
     x.zero_()
     lqdd.lq_solve(ctx, fp64, db, x)            # allocate the FP64 workspace
+    x.zero_()
+    lqdd.lq_solve(ctx, df64, db, x)            # and the df64 one
     times = {}
-    for name, prm in (("fp64", fp64), ("mixed", mixed)):
+    for name, prm in (("fp64", fp64), ("df64", df64), ("mixed", mixed)):
         best = None
         for _ in range(2):
             x.zero_()
@@ -349,22 +386,9 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
     roofline = None
     if dom:
-        name, d = dom
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        tps = traffic_per_site(name)
-        per_launch_sites = Vh
-        roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                    "peak_src": f"{pk['src']} hbm_gbs (STREAM-style copy)",
-                    "traffic": (tps * per_launch_sites) if tps else None,
-                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                    "avg_launch_us": round(1e3 * d["ms"] / d["launches"], 2)}
-    ops = {}
-    for k in ("hop_k1_f32", "hop_k2_f32", "hop_k1_f64", "hop_k2_f64"):
-        if k in prof and prof[k]["ms"] > 0:
-            ops[k] = {"gbs": round(prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9, 1),
-                      "frac": round(prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9 / pk["hbm_gbs"], 4),
-                      "avg_launch_us": round(1e3 * prof[k]["ms"] / prof[k]["launches"], 2)}
+        roofline = roofline_of(dom[0], dom[1], pk, Vh)
+        roofline["share_of_step"] = round(dom[1]["ms"] / ms, 4)
+    ops = {k: roofline_of(k, prof[k], pk, Vh) for k in sorted(prof) if prof[k]["ms"] > 0 and prof[k]["launches"]}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         g, n, dt, cores = oracle_ds_sample(args.cpu_seconds)
@@ -374,9 +398,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": "32^3x64 odd-even Wilson-clover step: set_gauge + 10 FP32 power iterations + "
-                               "Richardson(5) FP32 smoother + FGMRES(10) FP64 / GMRES(16) FP32 solve to 1e-10",
+                               "Richardson(5) FP32 smoother + FGMRES(10) df64 / GMRES(16) FP32 solve to 1e-10",
                    "lattice": list(L_WORK), "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC,
                    "l2": "inputs larger than L2 (gauge field 1.2 GB, each spinor field 0.4 GB); no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -390,9 +414,11 @@ def run_ours(args):
         "clocks": clk,
         "op": ops,
         "solve": {"mixed_ms": round(times["mixed"][0], 2), "fp64_ms": round(times["fp64"][0], 2),
+                  "df64_ms": round(times["df64"][0], 2),
                   "speedup": round(times["fp64"][0] / times["mixed"][0], 2),
-                  "mixed": times["mixed"][1], "fp64": times["fp64"][1],
-                  "status": {"mixed": times["mixed"][2], "fp64": times["fp64"][2]}},
+                  "speedup_vs_df64": round(times["df64"][0] / times["mixed"][0], 2),
+                  "mixed": times["mixed"][1], "fp64": times["fp64"][1], "df64": times["df64"][1],
+                  "status": {k: times[k][2] for k in times}},
         "kernels": prof,
         "step_bytes": step_bytes,
     }

@@ -59,7 +59,12 @@ typedef enum {
     LQ_ERR_STATE = 7           /* call out of order (e.g. an operator before lq_set_gauge) */
 } lq_status;
 
-typedef enum { LQ_F64 = 0, LQ_F32 = 1 } lq_prec;
+/* Arithmetic precisions.  LQ_DF64 is FP64-accurate "double-float" arithmetic:
+ * each real is an unevaluated sum of two floats (about 48 significand bits)
+ * combined with the error-free transformations of Knuth and Dekker, so it runs
+ * on the FP32 units, which GB300 provides at 64 times its FP64 rate; it meets
+ * the same 1e-12 parity bound as LQ_F64 with a float exponent range. */
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_DF64 = 2 } lq_prec;
 
 typedef enum {
     LQ_OP_FULL = 0,      /* D on the full lattice: in, out are full spinors */
@@ -83,8 +88,10 @@ typedef struct {
     int solver;          /* lq_solver_kind.  GMRES(m) on D_S (Algorithm 2), or flexible GMRES(m)
                             in FP64 right-preconditioned by the smoother (the outer solver of
                             Sec. 2.3) */
-    int prec;            /* lq_prec of a plain GMRES solve (ignored by FGMRES, whose outer
-                            iteration is always FP64) */
+    int prec;            /* lq_prec of the FP64-class steps: the plain GMRES solve (any lq_prec),
+                            the FGMRES outer iteration (LQ_F64 or LQ_DF64), and prepare,
+                            reconstruct and the true residual (LQ_F64 or LQ_DF64; LQ_F32 selects
+                            LQ_F64 there) */
     double tol;          /* stop when ||b_hat_e - D_S x_e|| <= tol ||b_hat_e|| (recomputed) */
     int restart;         /* Krylov length m of each cycle, 1..256 */
     int max_restarts;    /* maximum number of cycles, >= 1 */
@@ -182,6 +189,8 @@ typedef enum {
     LQ_K_NORM,           /* norms */
     LQ_K_FINISH,         /* second stage of the deterministic reductions */
     LQ_K_COPY,           /* device memset / memcpy steps (not kernels) */
+    LQ_K_HOP_K1_DF64, LQ_K_HOP_K2_DF64,   /* K1, K2 in df64 */
+    LQ_K_DOT_DF64, LQ_K_AXPY_DF64,        /* BLAS-1 in df64 */
     LQ_K_COUNT
 } lq_kernel_class;
 
@@ -190,9 +199,10 @@ typedef enum {
 lq_status lq_profile(lq_ctx *ctx, int on);
 
 /* Totals of the records of one kernel class since lq_profile(ctx, 1): launches,
- * summed device time in milliseconds and algorithmic bytes.  Synchronises.
- * Any output pointer may be NULL. */
-lq_status lq_profile_read(lq_ctx *ctx, int cls, long long *launches, double *ms, double *bytes);
+ * summed device time in milliseconds, algorithmic bytes and algorithmic flops
+ * (FP64-equivalent flops for df64 kernels).  Synchronises.  Any output pointer
+ * may be NULL. */
+lq_status lq_profile_read(lq_ctx *ctx, int cls, long long *launches, double *ms, double *bytes, double *flops);
 
 /* A static name for a kernel class ("" when out of range). */
 const char *lq_kernel_class_name(int cls);

@@ -6,8 +6,12 @@
 //    multi-axpy per pass, both over the whole basis) instead of the listing's
 //    modified Gram-Schmidt, so that each pass is one sweep over memory; the
 //    Hessenberg least-squares problem is solved by Givens rotations on the host.
-//  * Flexible GMRES(m) in FP64 (the outer solver of every level, Sec. 2.3),
-//    right-preconditioned by a Richardson or GMRES smoother in FP64 or FP32.
+//  * Flexible GMRES(m) in FP64 or df64 (the outer solver of every level,
+//    Sec. 2.3), right-preconditioned by a Richardson or GMRES smoother in
+//    FP64, df64 or FP32.
+// Precisions: native FP64, FP32, and df64 (FP64-accurate double-float
+// arithmetic on the FP32 units, several times faster than native FP64 on
+// GB300).
 //  * Richardson(n) on D_S (Algorithm 4) with the update fused into the second
 //    hopping kernel; the first sweep from x = 0 is x = omega b.
 //  * The odd-even smoother M_n (Sec. 2.4.5): prepare, smoother on D_S,
@@ -45,6 +49,9 @@ struct lq_ctx {
     void *C32[2] = {nullptr, nullptr};
     void *Ci64 = nullptr;
     void *Ci32 = nullptr;
+    void *Udf[2] = {nullptr, nullptr};
+    void *Cdf[2] = {nullptr, nullptr};
+    void *Cidf = nullptr;
     int *dflag = nullptr;
     RedScratch red{};
     double *h_pin = nullptr;   // pinned host mirror of red.out / coefficients
@@ -95,6 +102,9 @@ void *dev_alloc(lq_ctx *c, size_t bytes)
 {
     void *p = nullptr;
     ck(c, cudaMalloc(&p, bytes), "cudaMalloc");
+    // zero-fill: the BLAS kernels sweep whole fields and rely on the padding
+    // sites (cb >= V/2), which no kernel writes, staying zero
+    ck(c, cudaMemsetAsync(p, 0, bytes, c->st), "cudaMemsetAsync");
     c->owned.push_back(p);
     return p;
 }
@@ -115,14 +125,16 @@ void *ws(lq_ctx *c, const std::string &name, size_t bytes)
     return p;
 }
 
+const char *suffix(int prec) { return prec == P64 ? "/64" : prec == P32 ? "/32" : "/df"; }
+
 void *field(lq_ctx *c, int prec, const char *name)
 {
-    return ws(c, std::string(name) + (prec == P64 ? "/64" : "/32"), spinor_bytes(c->g, prec));
+    return ws(c, std::string(name) + suffix(prec), spinor_bytes(c->g, prec));
 }
 
 void *basis(lq_ctx *c, int prec, const char *name, int n)
 {
-    return ws(c, std::string(name) + (prec == P64 ? "/64" : "/32"), (size_t)n * spinor_bytes(c->g, prec));
+    return ws(c, std::string(name) + suffix(prec), (size_t)n * spinor_bytes(c->g, prec));
 }
 
 inline void *vec_at(lq_ctx *c, int prec, void *base, int j)
@@ -156,8 +168,12 @@ void need_gauge(lq_ctx *c)
     if (!c->have_gauge) fail(c, LQ_ERR_STATE, "no gauge field: call lq_set_gauge first");
 }
 
-const void *Cp(lq_ctx *c, int prec, int parity) { return prec == P64 ? c->C64[parity] : c->C32[parity]; }
-const void *Cip(lq_ctx *c, int prec) { return prec == P64 ? c->Ci64 : c->Ci32; }
+const void *Cp(lq_ctx *c, int prec, int parity)
+{
+    return prec == P64 ? c->C64[parity] : prec == P32 ? c->C32[parity] : c->Cdf[parity];
+}
+const void *Cip(lq_ctx *c, int prec) { return prec == P64 ? c->Ci64 : prec == P32 ? c->Ci32 : c->Cidf; }
+bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_DF64; }
 
 HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
 {
@@ -165,8 +181,7 @@ HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
     h.mode = mode;
     h.prec = prec;
     h.pout = pout;
-    h.U[0] = prec == P64 ? c->U64[0] : c->U32[0];
-    h.U[1] = prec == P64 ? c->U64[1] : c->U32[1];
+    for (int p = 0; p < 2; p++) h.U[p] = prec == P64 ? c->U64[p] : prec == P32 ? c->U32[p] : c->Udf[p];
     return h;
 }
 
@@ -447,31 +462,33 @@ long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void
     return 0;
 }
 
-// Flexible GMRES(m) in FP64, right-preconditioned by the smoother in inner_prec
+// Flexible GMRES(m) in precision W (FP64 or df64), right-preconditioned by the
+// smoother in inner_prec
 KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, long long *inner_iters)
 {
     Exec e = c->ex();
     KResult R;
     const int m = p->restart;
     const int q = p->inner_prec;
-    void *V = basis(c, P64, "outerV", m + 1);
-    void *Z = basis(c, P64, "outerZ", m);
-    void *t = field(c, P64, "outer:t");
-    void *vq = q == P64 ? nullptr : field(c, q, "prec:v");
-    void *zq = q == P64 ? nullptr : field(c, q, "prec:z");
-    const double bnorm = std::sqrt(norm2_of(c, P64, b));
+    const int W = p->prec;
+    void *V = basis(c, W, "outerV", m + 1);
+    void *Z = basis(c, W, "outerZ", m);
+    void *t = field(c, W, "outer:t");
+    void *vq = q == W ? nullptr : field(c, q, "prec:v");
+    void *zq = q == W ? nullptr : field(c, q, "prec:z");
+    const double bnorm = std::sqrt(norm2_of(c, W, b));
     if (!std::isfinite(bnorm)) fail(c, LQ_ERR_NAN, "NaN/Inf in the right-hand side");
     if (bnorm == 0.0) {
-        zero(e, P64, x);
+        zero(e, W, x);
         R.converged = true;
         return R;
     }
     Hess H(m);
     for (int cyc = 0; cyc < p->max_restarts; cyc++) {
-        void *v0 = vec_at(c, P64, V, 0);
-        op_schur(c, P64, x, v0, t);
-        axpby(e, P64, 1.0, 0.0, b, -1.0, 0.0, v0);
-        const double beta = std::sqrt(norm2_of(c, P64, v0));
+        void *v0 = vec_at(c, W, V, 0);
+        op_schur(c, W, x, v0, t);
+        axpby(e, W, 1.0, 0.0, b, -1.0, 0.0, v0);
+        const double beta = std::sqrt(norm2_of(c, W, v0));
         if (!std::isfinite(beta)) fail(c, LQ_ERR_NAN, "NaN/Inf in the residual");
         R.relres = beta / bnorm;
         if (beta <= p->tol * bnorm) {
@@ -479,22 +496,22 @@ KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lon
             return R;
         }
         R.cycles++;
-        axpby(e, P64, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
+        axpby(e, W, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
         H.reset(beta);
         int nk = 0;
         for (int k = 0; k < m; k++) {
-            void *vk = vec_at(c, P64, V, k);
-            void *zk = vec_at(c, P64, Z, k);
-            if (q == P64) {
-                *inner_iters += smoother_schur(c, p, P64, vk, zk);
+            void *vk = vec_at(c, W, V, k);
+            void *zk = vec_at(c, W, Z, k);
+            if (q == W) {
+                *inner_iters += smoother_schur(c, p, W, vk, zk);
             } else {
-                convert(e, P64, vk, q, vq);
+                convert(e, W, vk, q, vq);
                 *inner_iters += smoother_schur(c, p, q, vq, zq);
-                convert(e, q, zq, P64, zk);
+                convert(e, q, zq, W, zk);
             }
-            void *w = vec_at(c, P64, V, k + 1);
-            op_schur(c, P64, zk, w, t);
-            const double hk1 = arnoldi_cgs2(c, P64, V, k, w, H);
+            void *w = vec_at(c, W, V, k + 1);
+            op_schur(c, W, zk, w, t);
+            const double hk1 = arnoldi_cgs2(c, W, V, k, w, H);
             double colnorm2 = hk1 * hk1;
             for (int j = 0; j <= k; j++) colnorm2 += std::norm(H.h(j, k));
             H.h(k + 1, k) = hk1;
@@ -504,17 +521,17 @@ KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lon
             R.relres = est / bnorm;
             const bool breakdown = hk1 <= 1e-14 * std::sqrt(colnorm2);
             if (breakdown || est <= p->tol * bnorm || k == m - 1) break;
-            axpby(e, P64, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
+            axpby(e, W, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
         }
         std::vector<cd> y = H.solve(nk);
         upload_coef(c, y);
-        multi_axpy(e, P64, Z, nk, c->d_coef, +1, x, nullptr, 0);
+        multi_axpy(e, W, Z, nk, c->d_coef, +1, x, nullptr, 0);
         ck_launch(c, "fgmres update");
     }
-    void *r = vec_at(c, P64, V, 0);
-    op_schur(c, P64, x, r, t);
-    axpby(e, P64, 1.0, 0.0, b, -1.0, 0.0, r);
-    R.relres = std::sqrt(norm2_of(c, P64, r)) / bnorm;
+    void *r = vec_at(c, W, V, 0);
+    op_schur(c, W, x, r, t);
+    axpby(e, W, 1.0, 0.0, b, -1.0, 0.0, r);
+    R.relres = std::sqrt(norm2_of(c, W, r)) / bnorm;
     R.converged = R.relres <= p->tol;
     return R;
 }
@@ -527,10 +544,12 @@ void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
         if (p->restart < 1 || p->restart > MAX_RESTART) fail(c, LQ_ERR_ARG, "restart out of range 1..256");
         if (p->max_restarts < 1) fail(c, LQ_ERR_ARG, "max_restarts < 1");
         if (!(p->tol > 0.0) || !std::isfinite(p->tol)) fail(c, LQ_ERR_ARG, "tol must be positive");
-        if (p->prec != LQ_F64 && p->prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad prec");
+        if (!valid_prec(p->prec)) fail(c, LQ_ERR_ARG, "bad prec");
+        if (p->solver == LQ_SOLVER_FGMRES && p->prec == LQ_F32)
+            fail(c, LQ_ERR_ARG, "the FGMRES outer iteration needs LQ_F64 or LQ_DF64");
     }
     if (p->smoother < LQ_SMOOTH_NONE || p->smoother > LQ_SMOOTH_GMRES) fail(c, LQ_ERR_ARG, "bad smoother");
-    if (p->inner_prec != LQ_F64 && p->inner_prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad inner_prec");
+    if (!valid_prec(p->inner_prec)) fail(c, LQ_ERR_ARG, "bad inner_prec");
     if (p->smoother != LQ_SMOOTH_NONE && p->smooth_n < 0) fail(c, LQ_ERR_ARG, "smooth_n < 0");
     if (p->smoother == LQ_SMOOTH_GMRES && (p->smooth_m < 1 || p->smooth_m > MAX_RESTART))
         fail(c, LQ_ERR_ARG, "smooth_m out of range 1..256");
@@ -646,15 +665,23 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
             }
             c->Ci64 = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
             c->Ci32 = dev_alloc(c, (size_t)2 * 9 * g.stride * 16);
+            for (int p = 0; p < 2; p++) {
+                c->Udf[p] = dev_alloc(c, (size_t)4 * 9 * g.stride * 16);
+                c->Cdf[p] = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
+            }
+            c->Cidf = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
         }
         c->have_gauge = false;
-        import_links(e, U, c->U64, c->U32);
-        clover_build(e, U, c->lat.csw, c->lat.m0, c->C64);
+        // links in all three precisions; clover and inverse built in df64 and
+        // rounded to the FP64 and FP32 copies
+        import_links(e, U, c->U64, c->U32, c->Udf);
+        const void *udf[2] = {c->Udf[0], c->Udf[1]};
+        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
-        clover_invert(e, c->C64[1], c->Ci64, c->dflag);
-        clover_to_f32(e, c->C64[0], c->C32[0]);
-        clover_to_f32(e, c->C64[1], c->C32[1]);
-        clover_to_f32(e, c->Ci64, c->Ci32);
+        clover_invert(e, c->Cdf[1], c->Cidf, c->dflag);
+        clover_round(e, c->Cdf[0], c->C64[0], c->C32[0]);
+        clover_round(e, c->Cdf[1], c->C64[1], c->C32[1]);
+        clover_round(e, c->Cidf, c->Ci64, c->Ci32);
         ck_launch(c, "set_gauge kernels");
         int flag = 0;
         ck(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "cudaMemcpyAsync");
@@ -668,7 +695,7 @@ lq_status lq_apply(lq_ctx *c, int op, int prec, const void *in, void *out)
 {
     return guarded(c, [&] {
         if (!in || !out) fail(c, LQ_ERR_ARG, "NULL field");
-        if (prec != LQ_F64 && prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad precision");
+        if (!valid_prec(prec)) fail(c, LQ_ERR_ARG, "bad precision");
         need_gauge(c);
         Exec e = c->ex();
         void *a = field(c, prec, "apply:a"), *b = field(c, prec, "apply:b");
@@ -740,7 +767,7 @@ lq_status lq_estimate_norm(lq_ctx *c, int prec, int iters, const void *v0, doubl
 {
     return guarded(c, [&] {
         if (!v0 || !out || iters < 1) fail(c, LQ_ERR_ARG, "bad argument");
-        if (prec != LQ_F64 && prec != LQ_F32) fail(c, LQ_ERR_ARG, "bad precision");
+        if (!valid_prec(prec)) fail(c, LQ_ERR_ARG, "bad precision");
         need_gauge(c);
         Exec e = c->ex();
         void *v = field(c, prec, "pow:v"), *w = field(c, prec, "pow:w");
@@ -783,21 +810,23 @@ lq_status lq_smooth(lq_ctx *c, const lq_solver_params *p, const void *r, void *e
         need_gauge(c);
         Exec e = c->ex();
         const int q = p->inner_prec;
-        void *re = field(c, P64, "sm:re"), *ro = field(c, P64, "sm:ro");
-        void *rh = field(c, P64, "sm:rh"), *t = field(c, P64, "sm:t");
-        void *ee = field(c, P64, "sm:ee"), *eodd = field(c, P64, "sm:eo");
-        import_full(e, P64, r, re, ro);
-        op_prepare(c, P64, re, ro, rh, t);
-        if (q == P64) {
-            smoother_schur(c, p, P64, rh, ee);
+        const int W = p->prec;
+        if (W != LQ_F64 && W != LQ_DF64) fail(c, LQ_ERR_ARG, "prec (prepare/reconstruct) must be LQ_F64 or LQ_DF64");
+        void *re = field(c, W, "sm:re"), *ro = field(c, W, "sm:ro");
+        void *rh = field(c, W, "sm:rh"), *t = field(c, W, "sm:t");
+        void *ee = field(c, W, "sm:ee"), *eodd = field(c, W, "sm:eo");
+        import_full(e, W, r, re, ro);
+        op_prepare(c, W, re, ro, rh, t);
+        if (q == W) {
+            smoother_schur(c, p, W, rh, ee);
         } else {
             void *rq = field(c, q, "sm:rq"), *eq = field(c, q, "sm:eq");
-            convert(e, P64, rh, q, rq);
+            convert(e, W, rh, q, rq);
             smoother_schur(c, p, q, rq, eq);
-            convert(e, q, eq, P64, ee);
+            convert(e, q, eq, W, ee);
         }
-        op_reconstruct(c, P64, ro, ee, eodd);
-        export_full(e, P64, ee, eodd, eo);
+        op_reconstruct(c, W, ro, ee, eodd);
+        export_full(e, W, ee, eodd, eo);
     });
 }
 
@@ -813,38 +842,40 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
         check_params(c, p, true);
         need_gauge(c);
         Exec e = c->ex();
-        void *be = field(c, P64, "sol:be"), *bo = field(c, P64, "sol:bo");
-        void *xe = field(c, P64, "sol:xe"), *xo = field(c, P64, "sol:xo");
-        void *bh = field(c, P64, "sol:bh"), *t = field(c, P64, "sol:t");
-        import_full(e, P64, b, be, bo);
-        import_full(e, P64, x, xe, xo);
-        op_prepare(c, P64, be, bo, bh, t);
+        // precision of prepare, reconstruct and the true residual: FP64 or df64
+        const int W = p->prec == LQ_F32 ? (int)P64 : p->prec;
+        void *be = field(c, W, "sol:be"), *bo = field(c, W, "sol:bo");
+        void *xe = field(c, W, "sol:xe"), *xo = field(c, W, "sol:xo");
+        void *bh = field(c, W, "sol:bh"), *t = field(c, W, "sol:t");
+        import_full(e, W, b, be, bo);
+        import_full(e, W, x, xe, xo);
+        op_prepare(c, W, be, bo, bh, t);
         KResult R;
         long long inner = 0;
         if (p->solver == LQ_SOLVER_GMRES) {
-            if (p->prec == LQ_F64) {
-                R = gmres(c, P64, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV");
+            if (p->prec != LQ_F32) {
+                R = gmres(c, W, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV");
             } else {
                 void *bq = field(c, P32, "sol:bq"), *xq = field(c, P32, "sol:xq");
-                convert(e, P64, bh, P32, bq);
-                convert(e, P64, xe, P32, xq);
+                convert(e, W, bh, P32, bq);
+                convert(e, W, xe, P32, xq);
                 R = gmres(c, P32, bq, xq, p->restart, p->max_restarts, p->tol, false, "outerV");
-                convert(e, P32, xq, P64, xe);
+                convert(e, P32, xq, W, xe);
             }
         } else {
             R = fgmres(c, p, bh, xe, &inner);
         }
-        op_reconstruct(c, P64, bo, xe, xo);
-        export_full(e, P64, xe, xo, x);
-        // true residual on the full lattice, FP64
-        void *ye = field(c, P64, "sol:ye"), *yo = field(c, P64, "sol:yo");
-        op_full(c, P64, xe, xo, ye, yo);
-        axpby(e, P64, 1.0, 0.0, be, -1.0, 0.0, ye);
-        axpby(e, P64, 1.0, 0.0, bo, -1.0, 0.0, yo);
-        norm2(e, P64, ye, c->red, 0);
-        norm2(e, P64, yo, c->red, 1);
-        norm2(e, P64, be, c->red, 2);
-        norm2(e, P64, bo, c->red, 3);
+        op_reconstruct(c, W, bo, xe, xo);
+        export_full(e, W, xe, xo, x);
+        // true residual on the full lattice, in W
+        void *ye = field(c, W, "sol:ye"), *yo = field(c, W, "sol:yo");
+        op_full(c, W, xe, xo, ye, yo);
+        axpby(e, W, 1.0, 0.0, be, -1.0, 0.0, ye);
+        axpby(e, W, 1.0, 0.0, bo, -1.0, 0.0, yo);
+        norm2(e, W, ye, c->red, 0);
+        norm2(e, W, yo, c->red, 1);
+        norm2(e, W, be, c->red, 2);
+        norm2(e, W, bo, c->red, 3);
         reduce_finish(e, c->red, 0, 4);
         ck_launch(c, "true residual");
         const double *hv = fetch(c, 0, 4);
@@ -890,13 +921,13 @@ lq_status lq_profile(lq_ctx *c, int on)
     return LQ_OK;
 }
 
-lq_status lq_profile_read(lq_ctx *c, int cls, long long *launches, double *ms, double *bytes)
+lq_status lq_profile_read(lq_ctx *c, int cls, long long *launches, double *ms, double *bytes, double *flops)
 {
     return guarded(c, [&] {
         if (cls < 0 || cls >= K_COUNT) fail(c, LQ_ERR_ARG, "bad kernel class");
         sync(c);
         long long n = 0;
-        double t = 0.0, b = 0.0;
+        double t = 0.0, b = 0.0, f = 0.0;
         for (const auto &r : c->prof.recs) {
             if (r.cls != cls) continue;
             float dt = 0.0f;
@@ -904,10 +935,12 @@ lq_status lq_profile_read(lq_ctx *c, int cls, long long *launches, double *ms, d
             n++;
             t += dt;
             b += r.bytes;
+            f += r.flops;
         }
         if (launches) *launches = n;
         if (ms) *ms = t;
         if (bytes) *bytes = b;
+        if (flops) *flops = f;
     });
 }
 
@@ -915,7 +948,8 @@ const char *lq_kernel_class_name(int cls)
 {
     static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
                                          "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
-                                         "norm", "reduce_finish", "copy"};
+                                         "norm", "reduce_finish", "copy", "hop_k1_df64", "hop_k2_df64",
+                                         "dot_df64", "axpy_df64"};
     return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 

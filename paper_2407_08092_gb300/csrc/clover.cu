@@ -1,5 +1,5 @@
 // Clover term on the device: build from the gauge field, LDL^+ inverse of the
-// 6x6 Hermitian blocks, FP32 copies and natural-layout export.
+// 6x6 Hermitian blocks, copies in the other precisions and natural export.
 //
 // C(x) = (4 + m0) + c_sw (i/4) sum_{mu != nu} sigma_mu_nu F_mu_nu(x)
 // (Sec. 2.3, Wilson-clover; the 6x6 block structure is the one Sec. 2.4.5
@@ -11,63 +11,62 @@
 // This follows from sigma_jk = -eps_jkl diag(s_l, s_l) and
 // sigma_j4 = diag(s_j, -s_j) for the basis g_k = [[0,-i s_k],[i s_k,0]],
 // g_4 = [[0,1],[1,0]].
+//
+// The library builds and inverts in df64 (FP64-accurate, on the FP32 units,
+// which GB300 runs at 64 times its FP64 rate) and derives the FP64 and FP32
+// copies by rounding.  The build is split in two launches: one thread per
+// (site, plane) computes the four leaves and F of that plane into a scratch
+// array, then one thread per site assembles the two 6x6 blocks.
 #include "lq_kernels.h"
 
 namespace lq {
 
+template <typename R>
 struct M3 {
-    cx<double> a[9];
+    cx<R> a[9];
 };
 
-__device__ __forceinline__ M3 m3_load(const double2 *__restrict__ U, long long site, int mu)
+// C = A B, A^+ B, A B^+ (kept out of line: in df64 each is ~1.6k instructions,
+// and one copy per call site would overflow the instruction cache)
+template <typename R>
+__device__ __noinline__ M3<R> mm(const M3<R> &A, const M3<R> &B)
 {
-    M3 m;
-    const double2 *p = U + (site * 4 + mu) * 9;
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        double2 t = __ldg(p + k);
-        m.a[k] = {t.x, t.y};
-    }
-    return m;
-}
-
-// A * B, A^+ * B, A * B^+
-__device__ __forceinline__ M3 mm(const M3 &A, const M3 &B)
-{
-    M3 C;
+    M3<R> C;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cx<double> acc = cmul(A.a[i * 3], B.a[j]);
+            cx<R> acc = cmul(A.a[i * 3], B.a[j]);
             acc = cfma(A.a[i * 3 + 1], B.a[3 + j], acc);
             acc = cfma(A.a[i * 3 + 2], B.a[6 + j], acc);
             C.a[i * 3 + j] = acc;
         }
     return C;
 }
-__device__ __forceinline__ M3 mdm(const M3 &A, const M3 &B)
+template <typename R>
+__device__ __noinline__ M3<R> mdm(const M3<R> &A, const M3<R> &B)
 {
-    M3 C;
+    M3<R> C;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cx<double> acc = cmulc(A.a[i], B.a[j]);
+            cx<R> acc = cmulc(A.a[i], B.a[j]);
             acc = cfmac(A.a[3 + i], B.a[3 + j], acc);
             acc = cfmac(A.a[6 + i], B.a[6 + j], acc);
             C.a[i * 3 + j] = acc;
         }
     return C;
 }
-__device__ __forceinline__ M3 mmd(const M3 &A, const M3 &B)
+template <typename R>
+__device__ __noinline__ M3<R> mmd(const M3<R> &A, const M3<R> &B)
 {
-    M3 C;
+    M3<R> C;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cx<double> acc = cmul(A.a[i * 3], cconj(B.a[j * 3]));
+            cx<R> acc = cmul(A.a[i * 3], cconj(B.a[j * 3]));
             acc = cfma(A.a[i * 3 + 1], cconj(B.a[j * 3 + 1]), acc);
             acc = cfma(A.a[i * 3 + 2], cconj(B.a[j * 3 + 2]), acc);
             C.a[i * 3 + j] = acc;
@@ -75,67 +74,90 @@ __device__ __forceinline__ M3 mmd(const M3 &A, const M3 &B)
     return C;
 }
 
-__device__ __forceinline__ long long lex_of(const Geom &g, const int c[4])
+// the link U_mu at coordinates c, read from the internal per-parity copies
+template <typename R>
+__device__ __forceinline__ M3<R> link_at(const Geom &g, const typename St<R>::vec *Ue,
+                                         const typename St<R>::vec *Uo, const int c[4], int mu)
 {
-    return c[0] + (long long)g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
+    const long long lex = c[0] + (long long)g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
+    const int parity = (c[0] + c[1] + c[2] + c[3]) & 1;
+    M3<R> m;
+    load_link(parity ? Uo : Ue, g.stride, mu, lex >> 1, m.a);
+    return m;
 }
 
-__device__ __forceinline__ long long shifted(const Geom &g, const int c0[4], int mu, int dmu, int nu,
-                                             int dnu)
+__device__ __forceinline__ void shifted(const Geom &g, const int c0[4], int mu, int dmu, int nu, int dnu, int c[4])
 {
-    int c[4] = {c0[0], c0[1], c0[2], c0[3]};
+    c[0] = c0[0];
+    c[1] = c0[1];
+    c[2] = c0[2];
+    c[3] = c0[3];
     c[mu] = (c[mu] + dmu + g.L[mu]) % g.L[mu];
     c[nu] = (c[nu] + dnu + g.L[nu]) % g.L[nu];
-    return lex_of(g, c);
 }
 
-// F = (Q - Q^+)/8 for the plane (mu, nu) at site c
-__device__ void field_strength(const Geom &g, const double2 *__restrict__ U, const int c[4], int mu,
-                               int nu, M3 &F)
+// F = (Q - Q^+)/8 for the plane (mu, nu) at site c; Q = the four leaves
+template <typename R>
+__device__ void field_strength(const Geom &g, const typename St<R>::vec *Ue, const typename St<R>::vec *Uo,
+                               const int c[4], int mu, int nu, M3<R> &F)
 {
-    const long long x = lex_of(g, c);
-    const long long xpm = shifted(g, c, mu, 1, nu, 0), xpn = shifted(g, c, mu, 0, nu, 1);
-    const long long xmm = shifted(g, c, mu, -1, nu, 0), xmn = shifted(g, c, mu, 0, nu, -1);
-    const long long xmmpn = shifted(g, c, mu, -1, nu, 1), xmmmn = shifted(g, c, mu, -1, nu, -1);
-    const long long xpmmn = shifted(g, c, mu, 1, nu, -1);
-    M3 Q, T;
+    int xpm[4], xpn[4], xmm[4], xmn[4], xmmpn[4], xmmmn[4], xpmmn[4];
+    shifted(g, c, mu, 1, nu, 0, xpm);
+    shifted(g, c, mu, 0, nu, 1, xpn);
+    shifted(g, c, mu, -1, nu, 0, xmm);
+    shifted(g, c, mu, 0, nu, -1, xmn);
+    shifted(g, c, mu, -1, nu, 1, xmmpn);
+    shifted(g, c, mu, -1, nu, -1, xmmmn);
+    shifted(g, c, mu, 1, nu, -1, xpmmn);
+    M3<R> Q, T;
     // +mu +nu -mu -nu
-    T = mm(m3_load(U, x, mu), m3_load(U, xpm, nu));
-    T = mmd(T, m3_load(U, xpn, mu));
-    Q = mmd(T, m3_load(U, x, nu));
+    T = mm(link_at<R>(g, Ue, Uo, c, mu), link_at<R>(g, Ue, Uo, xpm, nu));
+    T = mmd(T, link_at<R>(g, Ue, Uo, xpn, mu));
+    Q = mmd(T, link_at<R>(g, Ue, Uo, c, nu));
     // +nu -mu -nu +mu
-    T = mmd(m3_load(U, x, nu), m3_load(U, xmmpn, mu));
-    T = mmd(T, m3_load(U, xmm, nu));
-    T = mm(T, m3_load(U, xmm, mu));
+    T = mmd(link_at<R>(g, Ue, Uo, c, nu), link_at<R>(g, Ue, Uo, xmmpn, mu));
+    T = mmd(T, link_at<R>(g, Ue, Uo, xmm, nu));
+    T = mm(T, link_at<R>(g, Ue, Uo, xmm, mu));
 #pragma unroll
     for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
     // -mu -nu +mu +nu:  U_mu(x-mu)^+ U_nu(x-mu-nu)^+ = (U_nu(x-mu-nu) U_mu(x-mu))^+
-    T = mm(m3_load(U, xmmmn, nu), m3_load(U, xmm, mu));
-    T = mdm(T, m3_load(U, xmmmn, mu));
-    T = mm(T, m3_load(U, xmn, nu));
+    T = mm(link_at<R>(g, Ue, Uo, xmmmn, nu), link_at<R>(g, Ue, Uo, xmm, mu));
+    T = mdm(T, link_at<R>(g, Ue, Uo, xmmmn, mu));
+    T = mm(T, link_at<R>(g, Ue, Uo, xmn, nu));
 #pragma unroll
     for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
     // -nu +mu +nu -mu
-    T = mdm(m3_load(U, xmn, nu), m3_load(U, xmn, mu));
-    T = mm(T, m3_load(U, xpmmn, nu));
-    T = mmd(T, m3_load(U, x, mu));
+    T = mdm(link_at<R>(g, Ue, Uo, xmn, nu), link_at<R>(g, Ue, Uo, xmn, mu));
+    T = mm(T, link_at<R>(g, Ue, Uo, xpmmn, nu));
+    T = mmd(T, link_at<R>(g, Ue, Uo, c, mu));
 #pragma unroll
     for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
+    const R eighth = R(0.125);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<double> q = Q.a[i * 3 + j], qt = cconj(Q.a[j * 3 + i]);
-            F.a[i * 3 + j] = 0.125 * (q - qt);
-        }
+        for (int j = 0; j < 3; j++) F.a[i * 3 + j] = eighth * (Q.a[i * 3 + j] - cconj(Q.a[j * 3 + i]));
 }
 
-__global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2 *__restrict__ U,
-                                                           double csw, double m0, double2 *Ce,
-                                                           double2 *Co)
+__device__ __forceinline__ void store_pair(double2 *p, double a, double b) { *p = make_double2(a, b); }
+__device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.hi, a.lo, b.hi, b.lo}; }
+__device__ __forceinline__ bool positive(double d) { return d > 0.0; }
+__device__ __forceinline__ bool positive(df64 d) { return df_positive(d); }
+
+// Field strength of one plane at one site per thread: F = (Q - Q^+)/8 is
+// anti-Hermitian, so 9 reals describe it: Im F_aa (a = 0,1,2), then F_01, F_02,
+// F_12 (re, im).  Stored as df64 pairs in F[plane][9][V].
+__constant__ int c_pmu[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int c_pnu[6] = {1, 2, 2, 3, 3, 3};
+
+template <typename R>
+__global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const typename St<R>::vec *__restrict__ Ue,
+                                                           const typename St<R>::vec *__restrict__ Uo, float2 *Fb)
 {
-    long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (lex >= g.V) return;
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= 6 * g.V) return;
+    const int p = (int)(id / g.V);
+    const long long lex = id - p * g.V;
     int c[4];
     {
         long long r = lex;
@@ -143,141 +165,158 @@ __global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2
         c[1] = (int)(r % g.L[1]); r /= g.L[1];
         c[2] = (int)(r % g.L[2]); c[3] = (int)(r / g.L[2]);
     }
-    const int parity = (c[0] + c[1] + c[2] + c[3]) & 1;
+    M3<R> F;
+    field_strength<R>(g, Ue, Uo, c, c_pmu[p], c_pnu[p], F);
+    const R v[9] = {F.a[0].im, F.a[4].im, F.a[8].im, F.a[1].re, F.a[1].im, F.a[2].re, F.a[2].im, F.a[5].re, F.a[5].im};
+#pragma unroll
+    for (int k = 0; k < 9; k++) Fb[((long long)p * 9 + k) * g.V + lex] = make_float2(v[k].hi, v[k].lo);
+}
+
+// entry (a, b) of the anti-Hermitian F of plane p at site lex
+__device__ __forceinline__ cx<df64> f_entry(const float2 *__restrict__ Fb, long long V, long long lex, int p, int a,
+                                            int b)
+{
+    auto ld = [&](int k) {
+        const float2 t = __ldg(Fb + ((long long)p * 9 + k) * V + lex);
+        return df64(t.x, t.y);
+    };
+    if (a == b) return {df64(0.0f, 0.0f), ld(a)};
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const int k = 3 + 2 * (lo == 0 ? hi - 1 : 2);   // (0,1) -> 3, (0,2) -> 5, (1,2) -> 7
+    const cx<df64> u = {ld(k), ld(k + 1)};
+    return a < b ? u : cx<df64>{-u.re, u.im};       // F_ba = -conj(F_ab)
+}
+
+// Assemble the two packed 6x6 blocks of C(x) from the six field strengths:
+// block b: G1 = -F_yz +- F_xt, G2 = F_xz +- F_yt, G3 = -F_xy +- F_zt (+ for b = 0),
+// M = i h [[G3, G1 - i G2], [G1 + i G2, -G3]], h = c_sw / 2, C = (4 + m0) + M.
+__global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const float2 *__restrict__ Fb, double csw,
+                                                              double m0, df2 *Ce, df2 *Co)
+{
+    const long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (lex >= g.V) return;
+    long long r = lex;
+    const int c0 = (int)(r % g.L[0]); r /= g.L[0];
+    const int c1 = (int)(r % g.L[1]); r /= g.L[1];
+    const int c2 = (int)(r % g.L[2]); const int c3 = (int)(r / g.L[2]);
+    const int parity = (c0 + c1 + c2 + c3) & 1;
     const long long cb = lex >> 1;
-    double2 *C = parity ? Co : Ce;
-
-    // G[blk][l] for l = 1,2,3 (0-based 0..2)
-    M3 G[2][3];
-#pragma unroll
-    for (int b = 0; b < 2; b++)
-#pragma unroll
-        for (int l = 0; l < 3; l++)
-#pragma unroll
-            for (int k = 0; k < 9; k++) G[b][l].a[k] = {0.0, 0.0};
-
-    // planes: (mu,nu), the G it feeds and the sign of the space-space term;
-    // time-plane terms enter block 0 with + and block 1 with -.
-    // G1 = -F_yz +- F_xt ; G2 = F_xz +- F_yt ; G3 = -F_xy +- F_zt
-    const int pmu[6] = {0, 0, 1, 0, 1, 2};
-    const int pnu[6] = {1, 2, 2, 3, 3, 3};
-    const int gl[6] = {2, 1, 0, 0, 1, 2};
-    const double sgn[6] = {-1.0, 1.0, -1.0, 1.0, 1.0, 1.0};
-    for (int p = 0; p < 6; p++) {
-        M3 F;
-        field_strength(g, U, c, pmu[p], pnu[p], F);
-        const bool time_plane = pnu[p] == 3;
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            G[0][gl[p]].a[k] = G[0][gl[p]].a[k] + sgn[p] * F.a[k];
-            const double s1 = time_plane ? -sgn[p] : sgn[p];
-            G[1][gl[p]].a[k] = G[1][gl[p]].a[k] + s1 * F.a[k];
-        }
-    }
-
-    const double diag = 4.0 + m0;
-    const double h = 0.5 * csw;   // (i c_sw / 2) * ...
+    df2 *C = parity ? Co : Ce;
+    const df64 diag(4.0 + m0), h(0.5 * csw);
+#pragma unroll 1
     for (int b = 0; b < 2; b++) {
-        // M = i h [[G3, G1 - i G2], [G1 + i G2, -G3]]
-        double r[36];
+        const bool plus = b == 0;
+        // G_l entries (a, c) for this block
+        auto G = [&](int l, int a, int cc) {
+            const int ps = l == 0 ? 2 : l == 1 ? 1 : 0;   // space plane: yz, xz, xy
+            const int pt = l == 0 ? 3 : l == 1 ? 4 : 5;   // time plane: xt, yt, zt
+            const cx<df64> fs = f_entry(Fb, g.V, lex, ps, a, cc), ft = f_entry(Fb, g.V, lex, pt, a, cc);
+            const cx<df64> s = l == 1 ? fs : -fs;
+            return plus ? s + ft : s - ft;
+        };
+        df64 out[36];
+#pragma unroll 1
         for (int i = 0; i < 6; i++) {
             const int si = i / 3, ai = i % 3;
-            cx<double> gd = G[b][2].a[ai * 3 + ai];
-            double v = -h * gd.im;      // Re(i h G3_aa) = -h Im(G3_aa)
-            r[i] = diag + (si == 0 ? v : -v);
+            const df64 v = -(h * G(2, ai, ai).im);          // Re(i h G3_aa) = -h Im(G3_aa)
+            out[i] = si == 0 ? diag + v : diag - v;
         }
+#pragma unroll 1
         for (int i = 1; i < 6; i++)
             for (int j = 0; j < i; j++) {
                 const int si = i / 3, ai = i % 3, sj = j / 3, aj = j % 3;
-                cx<double> m;
+                cx<df64> m;
                 if (si == sj) {
-                    cx<double> g3 = G[b][2].a[ai * 3 + aj];
-                    m = ti(h * g3);
+                    m = ti(h * G(2, ai, aj));
                     if (si == 1) m = -m;
                 } else {   // si = 1, sj = 0: i h (G1 + i G2)
-                    cx<double> g1 = G[b][0].a[ai * 3 + aj], g2 = G[b][1].a[ai * 3 + aj];
-                    m = ti(h * (g1 + ti(g2)));
+                    m = ti(h * (G(0, ai, aj) + ti(G(1, ai, aj))));
                 }
                 const int k = 6 + 2 * tri(i, j);
-                r[k] = m.re;
-                r[k + 1] = m.im;
+                out[k] = m.re;
+                out[k + 1] = m.im;
             }
-        for (int k = 0; k < 18; k++) C[(b * 18 + k) * g.stride + cb] = make_double2(r[2 * k], r[2 * k + 1]);
+#pragma unroll
+        for (int k = 0; k < 18; k++) store_pair(C + (b * 18 + k) * g.stride + cb, out[2 * k], out[2 * k + 1]);
     }
 }
 
 // LDL^+ factorisation and inverse of one packed Hermitian 6x6 block.
 // A = L D L^+ (L unit lower, D real); A^{-1} = L^{-+} D^{-1} L^{-1}.
-__global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const double2 *__restrict__ C,
-                                                            double2 *Ci, int *flag)
+template <typename R>
+__global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const typename St<R>::vec *__restrict__ C,
+                                                            typename St<R>::vec *Ci, int *flag)
 {
     long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 2 * g.Vh) return;
     const int b = (int)(id / g.Vh);
     const long long s = id - b * g.Vh;
-    double r[36];
-    for (int k = 0; k < 18; k++) {
-        double2 t = C[(b * 18 + k) * g.stride + s];
-        r[2 * k] = t.x;
-        r[2 * k + 1] = t.y;
-    }
-    cx<double> Lm[6][6];
-    double D[6];
+    R r[36];
+    load_block(C, g.stride, b, s, r);
+    cx<R> Lm[6][6];
+    R D[6];
     for (int i = 0; i < 6; i++)
-        for (int j = 0; j < 6; j++) Lm[i][j] = {i == j ? 1.0 : 0.0, 0.0};
+        for (int j = 0; j < 6; j++) Lm[i][j] = {R(i == j ? 1.0 : 0.0), R(0.0)};
     bool bad = false;
     for (int j = 0; j < 6; j++) {
-        double d = r[j];
-        for (int k = 0; k < j; k++) d -= (Lm[j][k].re * Lm[j][k].re + Lm[j][k].im * Lm[j][k].im) * D[k];
-        if (!(d > 0.0)) bad = true;   // Hermitian positive definite expected; NaN fails too
+        R d = r[j];
+        for (int k = 0; k < j; k++) d = d - (Lm[j][k].re * Lm[j][k].re + Lm[j][k].im * Lm[j][k].im) * D[k];
+        if (!positive(d)) bad = true;   // Hermitian positive definite expected; NaN fails too
         D[j] = d;
-        const double dinv = 1.0 / d;
+        const R dinv = R(1.0) / d;
         for (int i = j + 1; i < 6; i++) {
             const int kk = 6 + 2 * tri(i, j);
-            cx<double> a = {r[kk], r[kk + 1]};
+            cx<R> a = {r[kk], r[kk + 1]};
             for (int k = 0; k < j; k++) a = a - D[k] * cmul(Lm[i][k], cconj(Lm[j][k]));
             Lm[i][j] = dinv * a;
         }
     }
     // X = L^{-1} (unit lower) by forward substitution
-    cx<double> X[6][6];
+    cx<R> X[6][6];
     for (int i = 0; i < 6; i++)
-        for (int j = 0; j < 6; j++) X[i][j] = {i == j ? 1.0 : 0.0, 0.0};
+        for (int j = 0; j < 6; j++) X[i][j] = {R(i == j ? 1.0 : 0.0), R(0.0)};
     for (int i = 1; i < 6; i++)
         for (int j = 0; j < i; j++) {
-            cx<double> acc = {0.0, 0.0};
+            cx<R> acc = {R(0.0), R(0.0)};
             for (int k = j; k < i; k++) acc = cfma(Lm[i][k], X[k][j], acc);
             X[i][j] = -acc;
         }
+    R Dinv[6];
+    for (int k = 0; k < 6; k++) Dinv[k] = R(1.0) / D[k];
     // A^{-1}_{ij} = sum_{k >= max(i,j)} conj(X_ki) X_kj / D_k  (lower part, i >= j)
-    double out[36];
+    R out[36];
     for (int i = 0; i < 6; i++) {
-        double acc = 0.0;
-        for (int k = i; k < 6; k++) acc += (X[k][i].re * X[k][i].re + X[k][i].im * X[k][i].im) / D[k];
+        R acc = R(0.0);
+        for (int k = i; k < 6; k++) acc = acc + (X[k][i].re * X[k][i].re + X[k][i].im * X[k][i].im) * Dinv[k];
         out[i] = acc;
     }
     for (int i = 1; i < 6; i++)
         for (int j = 0; j < i; j++) {
-            cx<double> acc = {0.0, 0.0};
-            for (int k = i; k < 6; k++) acc = acc + (1.0 / D[k]) * cmulc(X[k][i], X[k][j]);
+            cx<R> acc = {R(0.0), R(0.0)};
+            for (int k = i; k < 6; k++) acc = acc + Dinv[k] * cmulc(X[k][i], X[k][j]);
             const int kk = 6 + 2 * tri(i, j);
             out[kk] = acc.re;
             out[kk + 1] = acc.im;
         }
-    for (int k = 0; k < 18; k++) Ci[(b * 18 + k) * g.stride + s] = make_double2(out[2 * k], out[2 * k + 1]);
+    for (int k = 0; k < 18; k++) store_pair(Ci + (b * 18 + k) * g.stride + s, out[2 * k], out[2 * k + 1]);
     if (bad) atomicAdd(flag, 1);
 }
 
-__global__ void clover_f32_kernel(Geom g, const double2 *__restrict__ C, float4 *C32)
+// df64 packed blocks of one parity -> FP64 and FP32 copies (rounding)
+__global__ void clover_round_kernel(Geom g, const df2 *__restrict__ Cdf, double2 *C64, float4 *C32)
 {
     long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 2 * g.Vh) return;
     const int b = (int)(id / g.Vh);
     const long long s = id - b * g.Vh;
     for (int k = 0; k < 9; k++) {
-        double2 u = C[(b * 18 + 2 * k) * g.stride + s];
-        double2 v = C[(b * 18 + 2 * k + 1) * g.stride + s];
-        C32[(b * 9 + k) * g.stride + s] = make_float4((float)u.x, (float)u.y, (float)v.x, (float)v.y);
+        const df2 u = Cdf[(b * 18 + 2 * k) * g.stride + s];
+        const df2 v = Cdf[(b * 18 + 2 * k + 1) * g.stride + s];
+        const double2 du = make_double2((double)u.rh + (double)u.rl, (double)u.ih + (double)u.il);
+        const double2 dv = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+        C64[(b * 18 + 2 * k) * g.stride + s] = du;
+        C64[(b * 18 + 2 * k + 1) * g.stride + s] = dv;
+        C32[(b * 9 + k) * g.stride + s] = make_float4((float)du.x, (float)du.y, (float)dv.x, (float)dv.y);
     }
 }
 
@@ -314,24 +353,33 @@ __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, con
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-void clover_build(const Exec &e, const void *U_nat, double csw, double m0, void *C64[2])
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *Fscratch)
 {
-    Launch L_(e, K_CLOVER, (double)e.g.V * (4 * 9 * 16 + 72 * 8));
-    clover_build_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(
-        e.g, (const double2 *)U_nat, csw, m0, (double2 *)C64[0], (double2 *)C64[1]);
+    {
+        // per (site, plane): 12 complex 3x3 products of 198 flops, the leaf sum
+        // and (Q - Q^+)/8
+        Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 16 * 144 + 6 * 72), (double)e.g.V * 6 * (12 * 198 + 54 + 36));
+        clover_field_kernel<df64><<<blocks_for(6 * e.g.V, 128), 128, 0, e.st>>>(e.g, (const df2 *)Udf[0],
+                                                                                (const df2 *)Udf[1],
+                                                                                (float2 *)Fscratch);
+    }
+    Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * 8));
+    clover_assemble_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(e.g, (const float2 *)Fscratch, csw, m0,
+                                                                     (df2 *)Cdf[0], (df2 *)Cdf[1]);
 }
 
-void clover_invert(const Exec &e, const void *C64, void *Cinv64, int *flag)
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag)
 {
-    Launch L_(e, K_CLOVER, (double)e.g.Vh * 2 * 72 * 8);
-    clover_invert_kernel<<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(e.g, (const double2 *)C64,
-                                                                        (double2 *)Cinv64, flag);
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 2 * 72 * 8, (double)e.g.Vh * 2 * 1500);
+    clover_invert_kernel<df64><<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(e.g, (const df2 *)Cdf,
+                                                                              (df2 *)Cidf, flag);
 }
 
-void clover_to_f32(const Exec &e, const void *C64, void *C32)
+void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32)
 {
-    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 4));
-    clover_f32_kernel<<<blocks_for(2 * e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)C64, (float4 *)C32);
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 8 + 4));
+    clover_round_kernel<<<blocks_for(2 * e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const df2 *)Cdf, (double2 *)C64,
+                                                                      (float4 *)C32);
 }
 
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out)

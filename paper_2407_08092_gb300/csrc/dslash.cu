@@ -15,6 +15,8 @@
 //   (1 - s g_k) psi = (h, s(-i s_k) h)  with h = psi_u + s i s_k psi_l   (k = 1,2,3)
 //   (1 - s g_4) psi = (h, -s h)         with h = psi_u - s psi_l
 // where s = +1 for the forward and -1 for the backward hop.
+#include <type_traits>
+
 #include "lq_kernels.h"
 
 namespace lq {
@@ -197,6 +199,153 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> 
     store_spinor(k.out, st, s, v);
 }
 
+// ---------------------------------------------------------------------------
+// df64 variant.  Each df64 operation is a chain of several FP32 instructions,
+// so the fully unrolled eight-direction body of hop_kernel would not fit the
+// instruction cache.  Here the eight hops share one loop body: the spin
+// projection and reconstruction of direction d are the table entries
+//   h0 = psi_0 + i^qa psi_pa,  h1 = psi_1 + i^qb psi_(5-pa)
+//   acc_2 += i^qc u_ra,        acc_3 += i^qd u_(1-ra)
+// (the same identities as `project` / `reconstruct` above, with s = -1 for the
+// forward and +1 for the backward hop), and the backward link enters as U^+.
+// ---------------------------------------------------------------------------
+// y = C x for both 6x6 blocks, one shared loop body (register arrays are
+// selected, never indexed by the loop variable)
+__device__ __forceinline__ void clover_apply_df(const df2 *__restrict__ C, long long stride, long long s,
+                                                const cx<df64> x[12], cx<df64> y[12])
+{
+#pragma unroll 1
+    for (int blk = 0; blk < 2; blk++) {
+        cx<df64> xi[6], yo[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) xi[i] = blk ? x[6 + i] : x[i];
+        df64 a[36];
+        load_block(C, stride, blk, s, a);
+        herm6_apply<df64>(a, xi, yo);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            if (blk) y[6 + i] = yo[i];
+            else y[i] = yo[i];
+        }
+    }
+}
+
+__device__ __forceinline__ cx<df64> rot_i(cx<df64> z, int q)   // i^q z
+{
+    const cx<df64> a = (q & 1) ? cx<df64>{-z.im, z.re} : z;
+    return (q & 2) ? cx<df64>{-a.re, -a.im} : a;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
+{
+    // per direction d = 2 mu + (backward): the partner of h0 is psi_3 for x, y
+    // and psi_2 for z, t (acc_2 takes u_1 resp. u_0); the i-powers
+    //   qa = {1,3,0,2,1,3,2,0}, qb = {1,3,2,0,3,1,2,0},
+    //   qc = {3,1,2,0,3,1,2,0}, qd = {3,1,0,2,1,3,2,0}
+    // are packed two bits per direction (no local-memory tables)
+    constexpr unsigned QA = 11661u, QB = 10029u, QC = 10023u, QD = 11655u;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+    const long long st = g.stride;
+    cx<df64> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+
+#pragma unroll 1
+    for (int d = 0; d < 8; d++) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        long long nb;
+        bool flip = false;
+        if (mu == 0) {
+            const int xn = fwd ? (c.x + 1 == g.L[0] ? 0 : c.x + 1) : (c.x == 0 ? g.L[0] - 1 : c.x - 1);
+            nb = c.row * g.Lxh + (xn >> 1);
+        } else {
+            const int coord = mu == 1 ? c.y : mu == 2 ? c.z : c.t;
+            const int ext = g.L[mu];
+            const long long dd = mu == 1 ? (long long)g.Lxh
+                               : mu == 2 ? (long long)g.Lxh * g.L[1] : (long long)g.Lxh * g.L[1] * g.L[2];
+            if (fwd) nb = (coord + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd;
+            else nb = (coord == 0) ? s + (long long)(ext - 1) * dd : s - dd;
+            if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
+        }
+        cx<df64> p[12];
+        load_spinor(k.in, st, nb, p);
+        cx<df64> m[9];
+        load_link(fwd ? k.Uout : k.Uin, st, mu, fwd ? s : nb, m);
+        const int pa = d < 4 ? 3 : 2;
+        const int qa = (QA >> (2 * d)) & 3, qb = (QB >> (2 * d)) & 3;
+        cx<df64> h[6];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const cx<df64> q0 = pa == 3 ? p[9 + a] : p[6 + a];
+            const cx<df64> q1 = pa == 3 ? p[6 + a] : p[9 + a];
+            h[a] = p[a] + rot_i(q0, qa);
+            h[3 + a] = p[3 + a] + rot_i(q1, qb);
+        }
+        cx<df64> u[6];
+#pragma unroll
+        for (int hs = 0; hs < 2; hs++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                // row a of U (forward) or of U^+ (backward): entries m[a*3+b] or conj(m[b*3+a])
+                cx<df64> e0 = fwd ? m[a * 3 + 0] : cconj(m[0 * 3 + a]);
+                cx<df64> e1 = fwd ? m[a * 3 + 1] : cconj(m[1 * 3 + a]);
+                cx<df64> e2 = fwd ? m[a * 3 + 2] : cconj(m[2 * 3 + a]);
+                cx<df64> t = cmul(e0, h[hs * 3 + 0]);
+                t = cfma(e1, h[hs * 3 + 1], t);
+                t = cfma(e2, h[hs * 3 + 2], t);
+                u[hs * 3 + a] = flip ? -t : t;
+            }
+        const int ra = d < 4 ? 1 : 0;
+        const int qc = (QC >> (2 * d)) & 3, qd = (QD >> (2 * d)) & 3;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            acc[a] = acc[a] + u[a];
+            acc[3 + a] = acc[3 + a] + u[3 + a];
+            const cx<df64> v2 = ra ? u[3 + a] : u[a];
+            const cx<df64> v3 = ra ? u[a] : u[3 + a];
+            acc[6 + a] = acc[6 + a] + rot_i(v2, qc);
+            acc[9 + a] = acc[9 + a] + rot_i(v3, qd);
+        }
+    }
+
+    cx<df64> v[12];
+    const df64 half(0.5f, 0.0f), mhalf(-0.5f, 0.0f);
+    if (MODE == HOP_K1) {
+#pragma unroll
+        for (int i = 0; i < 12; i++) acc[i] = mhalf * acc[i];
+        clover_apply_df(k.clov, st, s, acc, v);
+    } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
+        cx<df64> x[12];
+        load_spinor_rw(k.in2, st, s, x);
+        clover_apply_df(k.clov, st, s, x, v);
+        const df64 f = MODE == HOP_FULL ? mhalf : half;
+#pragma unroll
+        for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
+        if (MODE == HOP_RICH) {
+            cx<df64> bb[12];
+            load_spinor(k.b, st, s, bb);
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = x[i] + k.omega * (bb[i] - v[i]);
+        }
+    } else {
+        cx<df64> y[12];
+        load_spinor_rw(k.in2, st, s, y);
+#pragma unroll
+        for (int i = 0; i < 12; i++) y[i] = y[i] + half * acc[i];
+        if (MODE == HOP_RECON) {
+            clover_apply_df(k.clov, st, s, y, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = y[i];
+        }
+    }
+    store_spinor(k.out, st, s, v);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) clover_mul_kernel(Geom g, const typename St<R>::vec *__restrict__ C,
                                                          const typename St<R>::vec *in, typename St<R>::vec *out)
@@ -221,19 +370,24 @@ static void launch_hop(const Exec &e, const HopCall &c)
     k.Uout = (const V *)c.U[c.pout];
     k.Uin = (const V *)c.U[1 - c.pout];
     k.clov = (const V *)c.clov;
-    k.omega = (R)c.omega;
+    k.omega = R(c.omega);
     k.pout = c.pout;
     const unsigned blocks = (unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS);
-    hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+    if constexpr (std::is_same<R, df64>::value)
+        hop_df_kernel<MODE><<<blocks, 128, 0, e.st>>>(e.g, k);
+    else
+        hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
 }
 
-// algorithmic bytes per output site of one hopping launch
+// algorithmic bytes per output site of one hopping launch (FP64 and df64 share
+// the 8-byte-per-real layout)
 static double hop_site_bytes(int mode, int prec)
 {
-    const double sp = prec == P64 ? 192.0 : 96.0;          // spinor
-    const double lk = prec == P64 ? 144.0 : 48.0;          // link (18 / 12 reals)
-    const double cl = prec == P64 ? 576.0 : 288.0;         // 72-real clover pair
-    double b = 8 * lk + sp + sp;                            // links, neighbours, output
+    const bool wide = prec != P32;
+    const double sp = wide ? 192.0 : 96.0;          // spinor
+    const double lk = wide ? 144.0 : 48.0;          // link (18 / 12 reals)
+    const double cl = wide ? 576.0 : 288.0;         // 72-real clover pair
+    double b = 8 * lk + sp + sp;                    // links, neighbours, output
     switch (mode) {
     case HOP_K1: b += cl; break;
     case HOP_K2: case HOP_FULL: b += sp + cl; break;
@@ -244,14 +398,28 @@ static double hop_site_bytes(int mode, int prec)
     return b;
 }
 
+static int hop_class(int mode, int prec)
+{
+    if (mode == HOP_K1) return prec == P64 ? K_HOP_K1_F64 : prec == P32 ? K_HOP_K1_F32 : K_HOP_K1_DF;
+    if (mode == HOP_K2 || mode == HOP_RICH) return prec == P64 ? K_HOP_K2_F64 : prec == P32 ? K_HOP_K2_F32 : K_HOP_K2_DF;
+    return K_HOP_OTHER;
+}
+
 void hop(const Exec &e, const HopCall &c)
 {
 #define LQ_CASE(M)                                                              \
     case M:                                                                     \
         if (c.prec == P64) launch_hop<double, M>(e, c);                         \
-        else launch_hop<float, M>(e, c);                                        \
+        else if (c.prec == P32) launch_hop<float, M>(e, c);                     \
+        else launch_hop<df64, M>(e, c);                                         \
         break;
-    Launch L_(e, (c.mode == HOP_K1 ? (c.prec == P64 ? K_HOP_K1_F64 : K_HOP_K1_F32) : (c.mode == HOP_K2 || c.mode == HOP_RICH) ? (c.prec == P64 ? K_HOP_K2_F64 : K_HOP_K2_F32) : K_HOP_OTHER), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec));
+    // algorithmic flops per site: 1320 for the eight hops (projection 12,
+    // two SU(3) mat-vecs 132, accumulation 24, per direction, less the first
+    // accumulation), 552 per clover-block pair, 24 per spinor add / scale
+    static const double hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
+                                        1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552};
+    Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec),
+              (double)e.g.Vh * hop_flops[c.mode]);
     switch (c.mode) {
         LQ_CASE(HOP_K1)
         LQ_CASE(HOP_K2)
@@ -265,14 +433,17 @@ void hop(const Exec &e, const HopCall &c)
 
 void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void *out)
 {
-    Launch L_(e, K_HOP_OTHER, (double)e.g.Vh * (prec == P64 ? 192.0 * 2 + 576.0 : 96.0 * 2 + 288.0));
+    Launch L_(e, K_HOP_OTHER, (double)e.g.Vh * (prec != P32 ? 192.0 * 2 + 576.0 : 96.0 * 2 + 288.0),
+              (double)e.g.Vh * 552);
     const unsigned blocks = (unsigned)((e.g.Vh + 255) / 256);
     if (prec == P64)
         clover_mul_kernel<double><<<blocks, 256, 0, e.st>>>(e.g, (const double2 *)clov, (const double2 *)in,
                                                            (double2 *)out);
-    else
+    else if (prec == P32)
         clover_mul_kernel<float><<<blocks, 256, 0, e.st>>>(e.g, (const float4 *)clov, (const float4 *)in,
                                                           (float4 *)out);
+    else
+        clover_mul_kernel<df64><<<blocks, 256, 0, e.st>>>(e.g, (const df2 *)clov, (const df2 *)in, (df2 *)out);
 }
 
 }  // namespace lq

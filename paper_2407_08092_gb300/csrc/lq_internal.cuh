@@ -37,6 +37,85 @@ struct Geom {
 };
 
 // ---------------------------------------------------------------------------
+// double-float ("df64") arithmetic: an unevaluated sum hi + lo of two floats,
+// |lo| <= ulp(hi)/2, carrying about 48 significand bits.  GB300 executes FP32
+// at 64 times its FP64 rate, so FP64-accurate work runs faster in this form.
+// Built from the error-free transformations of Knuth (TwoSum), Dekker 1971
+// (Fast2Sum, and the double-length add/multiply built on them) and the FMA
+// form of the exact product (p = a*b, e = fma(a, b, -p)).  The explicit _rn
+// intrinsics keep the compiler from contracting or reordering these steps.
+// ---------------------------------------------------------------------------
+struct df64 {
+    float hi, lo;
+    __host__ __device__ df64() {}
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ df64(double d)
+    {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
+};
+
+// s + e == a + b exactly, for |a| >= |b| (Dekker)
+__device__ __forceinline__ df64 df_fast2sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// s + e == a + b exactly (Knuth)
+__device__ __forceinline__ df64 df_2sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// p + e == a * b exactly (FMA)
+__device__ __forceinline__ df64 df_2prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return df64(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+{
+    df64 s = df_2sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return df_fast2sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+{
+    df64 p = df_2prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return df_fast2sum(p.hi, p.lo);
+}
+// a * b + c with one rounding of the combined low parts
+__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
+{
+    df64 p = df_2prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    df64 s = df_2sum(p.hi, c.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(p.lo, c.lo));
+    return df_fast2sum(s.hi, s.lo);
+}
+// keep the float and double fma overloads visible next to the df64 one, so
+// that templates never route FP64 or FP32 arithmetic through df64
+using ::fma;
+
+__device__ __forceinline__ df64 operator/(df64 a, df64 b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df64 r = a - b * df64(q1, 0.0f);
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return df_fast2sum(q1, q2);
+}
+__device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
+__device__ __forceinline__ bool df_positive(df64 a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
 // complex arithmetic
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -108,6 +187,20 @@ struct St<float> {
     static constexpr int LINK_VECS = 3;     // 12-real compressed links
 };
 
+// one df64 complex (or a pair of df64 reals) in 16 bytes: the df64 layouts
+// mirror the FP64 ones vector for vector
+struct __align__(16) df2 {
+    float rh, rl, ih, il;
+};
+
+template <>
+struct St<df64> {
+    typedef df2 vec;                   // one complex per vector
+    static constexpr int SPINOR_VECS = 12;
+    static constexpr int CLOVER_VECS = 18;
+    static constexpr int LINK_VECS = 9;     // 18-real links
+};
+
 template <typename R>
 __host__ __device__ constexpr long long spinor_elems(long long stride)
 {
@@ -117,6 +210,46 @@ __host__ __device__ constexpr long long spinor_elems(long long stride)
 // read-only cached vector loads
 __device__ __forceinline__ double2 ldg(const double2 *p) { return __ldg(p); }
 __device__ __forceinline__ float4 ldg(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ df2 ldg(const df2 *p)
+{
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    return df2{t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ cx<df64> df2_cx(df2 t) { return {df64(t.rh, t.rl), df64(t.ih, t.il)}; }
+__device__ __forceinline__ df2 cx_df2(cx<df64> v) { return df2{v.re.hi, v.re.lo, v.im.hi, v.im.lo}; }
+
+__device__ __forceinline__ void load_spinor(const df2 *__restrict__ p, long long stride, long long s,
+                                            cx<df64> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) v[c] = df2_cx(ldg(p + c * stride + s));
+}
+__device__ __forceinline__ void load_spinor_rw(const df2 *p, long long stride, long long s, cx<df64> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) v[c] = df2_cx(p[c * stride + s]);
+}
+__device__ __forceinline__ void store_spinor(df2 *p, long long stride, long long s, const cx<df64> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) p[c * stride + s] = cx_df2(v[c]);
+}
+__device__ __forceinline__ void load_link(const df2 *__restrict__ U, long long stride, int mu, long long s,
+                                          cx<df64> m[9])
+{
+#pragma unroll
+    for (int k = 0; k < 9; k++) m[k] = df2_cx(ldg(U + (mu * 9 + k) * stride + s));
+}
+__device__ __forceinline__ void load_block(const df2 *__restrict__ C, long long stride, int blk, long long s,
+                                           df64 r[36])
+{
+#pragma unroll
+    for (int k = 0; k < 18; k++) {
+        const df2 t = ldg(C + (blk * 18 + k) * stride + s);
+        r[2 * k] = df64(t.rh, t.rl);
+        r[2 * k + 1] = df64(t.ih, t.il);
+    }
+}
 
 __device__ __forceinline__ void load_spinor(const double2 *__restrict__ p, long long stride,
                                             long long s, cx<double> v[12])

@@ -9,13 +9,16 @@
 
 namespace lq {
 
-enum Prec { P64 = 0, P32 = 1 };
+// Internal precisions: native FP64, FP32, and double-float (df64: FP64-accurate
+// arithmetic on the FP32 units, stored as float pairs in the FP64 layouts).
+enum Prec { P64 = 0, P32 = 1, PDF = 2 };
 
 // Kernel classes for the per-class device timing (mirrors lq_kernel_class of
 // the public header).
 enum KClass {
     K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
-    K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY, K_COUNT
+    K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY,
+    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_COUNT
 };
 
 // Optional CUDA-event timing of every launch (enabled by lq_profile).
@@ -24,7 +27,7 @@ struct Prof {
     struct Rec {
         int cls;
         cudaEvent_t a, b;
-        double bytes;
+        double bytes, flops;
     };
     std::vector<cudaEvent_t> pool;
     size_t next = 0;
@@ -42,14 +45,16 @@ struct Exec {
 };
 
 // Accounts one launch: records a start event at construction and an end
-// event, the launch count and the algorithmic bytes at destruction.  Kernel
-// launches count toward `launches`; memset/memcpy steps (K_COPY) do not.
+// event, the launch count, the algorithmic bytes and the algorithmic flops
+// (FP64-equivalent for df64 kernels) at destruction.  Kernel launches count
+// toward `launches`; memset/memcpy steps (K_COPY) do not.
 struct Launch {
     const Exec &e;
     int cls;
-    double bytes;
+    double bytes, flops;
     cudaEvent_t a = nullptr;
-    Launch(const Exec &e_, int cls_, double bytes_) : e(e_), cls(cls_), bytes(bytes_)
+    Launch(const Exec &e_, int cls_, double bytes_, double flops_ = 0.0)
+        : e(e_), cls(cls_), bytes(bytes_), flops(flops_)
     {
         if (e.prof && e.prof->on) {
             a = e.prof->get();
@@ -63,7 +68,7 @@ struct Launch {
         if (a) {
             cudaEvent_t b = e.prof->get();
             cudaEventRecord(b, e.st);
-            e.prof->recs.push_back({cls, a, b, bytes});
+            e.prof->recs.push_back({cls, a, b, bytes, flops});
         }
     }
 };
@@ -71,12 +76,12 @@ struct Launch {
 // Bytes of one internal per-parity spinor field in a precision.
 inline size_t spinor_bytes(const Geom &g, int prec)
 {
-    return (size_t)24 * g.stride * (prec == P64 ? 8 : 4);
+    return (size_t)24 * g.stride * (prec == P32 ? 4 : 8);
 }
 
 // ---- layout (layout.cu) ----------------------------------------------------
 // natural complex-double gauge field -> per-parity internal link copies
-void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2]);
+void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2], void *Udf[2]);
 // natural half spinor [Vh][12] c128 <-> internal field of one parity
 void import_half(const Exec &e, int prec, const void *nat, void *f);
 void export_half(const Exec &e, int prec, const void *f, void *nat);
@@ -89,13 +94,14 @@ void convert(const Exec &e, int from, const void *in, int to, void *out);
 void gamma5(const Exec &e, int prec, const void *in, void *out);
 
 // ---- clover (clover.cu) ----------------------------------------------------
-// C(x) of every site from the natural gauge field, FP64 packed blocks per parity
-void clover_build(const Exec &e, const void *U_nat, double csw, double m0, void *C64[2]);
-// packed inverse of the blocks of one parity by LDL^+; *flag += failures
-void clover_invert(const Exec &e, const void *C64, void *Cinv64, int *flag);
-// FP64 -> FP32 copy of one parity's packed blocks
-void clover_to_f32(const Exec &e, const void *C64, void *C32);
-// natural export: out[V][2][6][6] c128 from packed blocks (null parity pointer -> zeros)
+// C(x) of every site from the internal df64 links, df64 packed blocks per parity;
+// Fscratch: device scratch of 6 * 9 * V * 8 bytes (the six field strengths)
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *Fscratch);
+// df64 packed inverse of the blocks of one parity by LDL^+; *flag += failures
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag);
+// df64 packed blocks of one parity -> rounded FP64 and FP32 copies
+void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32);
+// natural export: out[V][2][6][6] c128 from FP64 packed blocks (null parity pointer -> zeros)
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
 
 // ---- hopping term (dslash.cu) ----------------------------------------------
@@ -153,9 +159,6 @@ void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, co
 void norm2(const Exec &e, int prec, const void *w, const RedScratch &r, int slot);
 // sum the per-block partials of slots [first, first + count) into r.out
 void reduce_finish(const Exec &e, const RedScratch &r, int first, int count);
-// y = x * (1 / sqrt(r.out[2*slot])) with the norm read on the device
-void scale_by_inv_norm(const Exec &e, int prec, const void *x, const RedScratch &r, int slot,
-                       void *y);
 // norm of a natural c128 field of n sites (used by lq_norm2)
 void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch &r, int slot);
 int reduction_blocks(const Geom &g);

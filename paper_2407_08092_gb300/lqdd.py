@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblqdd.so")
 
 LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN, LQ_ERR_NAN, LQ_ERR_STATE = range(8)
-LQ_F64, LQ_F32 = 0, 1
+LQ_F64, LQ_F32, LQ_DF64 = 0, 1, 2
 LQ_OP_FULL, LQ_OP_SCHUR, LQ_OP_SCHUR_DAG, LQ_OP_EE, LQ_OP_OO_INV = range(5)
 LQ_SOLVER_GMRES, LQ_SOLVER_FGMRES = 0, 1
 LQ_SMOOTH_NONE, LQ_SMOOTH_RICHARDSON, LQ_SMOOTH_GMRES = 0, 1, 2
@@ -67,7 +67,8 @@ _lib.lq_export_clover.argtypes = [_P, ctypes.c_int, _P]
 _lib.lq_counters.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
 _lib.lq_profile.argtypes = [_P, ctypes.c_int]
 _lib.lq_profile_read.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
-                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
 _lib.lq_norm2_noalloc.argtypes = [_P, ctypes.c_longlong, _P, _P]
 _lib.lq_norm2_noalloc.restype = ctypes.c_int
 _lib.lq_kernel_class_name.argtypes = [ctypes.c_int]
@@ -204,7 +205,7 @@ def lq_counters(ctx):
     return n.value, b.value
 
 
-LQ_K_COUNT = 14
+LQ_K_COUNT = 18
 
 
 def lq_profile(ctx, on: bool) -> None:
@@ -212,12 +213,14 @@ def lq_profile(ctx, on: bool) -> None:
 
 
 def lq_profile_read(ctx, cls: int):
-    """(launches, milliseconds, algorithmic bytes) of one kernel class."""
+    """(launches, milliseconds, algorithmic bytes, algorithmic flops) of one kernel class."""
     n = ctypes.c_longlong()
     ms = ctypes.c_double()
     b = ctypes.c_double()
-    _check(ctx, _lib.lq_profile_read(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
-    return n.value, ms.value, b.value
+    f = ctypes.c_double()
+    _check(ctx, _lib.lq_profile_read(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
+                                     ctypes.byref(f)))
+    return n.value, ms.value, b.value, f.value
 
 
 def lq_kernel_class_name(cls: int) -> str:

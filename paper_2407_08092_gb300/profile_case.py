@@ -1,8 +1,10 @@
-"""A small, self-contained case of the hopping kernels for profiler captures.
+"""A small, self-contained case of the library's kernels for profiler captures.
 
 Builds a context on a seeded lattice (default 24^3 x 48, whose per-launch
-working set is larger than L2 but whose device footprint stays near 1.5 GB)
-and applies D_S (K1 + K2) `--apps` times in one precision through the C ABI:
+working set is larger than L2 but whose device footprint stays within a few
+GB) and then either applies D_S (K1 + K2) `--apps` times in one precision
+through the C ABI, or runs `--apps` mixed-precision solves (FGMRES(10) in
+df64 preconditioned by GMRES(16) in FP32), e.g.
 ``python -m paper_2407_08092_gb300.profile_case --lattice 24,24,24,48 --prec 1 --apps 3``.
 """
 import argparse
@@ -16,21 +18,35 @@ from paper_2407_08092_gb300 import lqdd, synth
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="24,24,24,48")
-    ap.add_argument("--prec", type=int, default=1)
+    ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32, 2 df64")
     ap.add_argument("--apps", type=int, default=3)
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
     a = ap.parse_args()
     L = tuple(int(v) for v in a.lattice.split(","))
     V = int(np.prod(L))
     ctx = lqdd.lq_create(lqdd.make_lattice(L, -1, 0.05, 1.0), torch.cuda.current_stream().cuda_stream)
     lqdd.lq_set_gauge(ctx, torch.from_numpy(synth.gauge_links(L, 0.25, 1003)).cuda())
-    n = V if a.op == lqdd.LQ_OP_FULL else V // 2
-    x = torch.from_numpy(synth.gaussian_spinor(n, 2003)).cuda()
-    y = torch.empty_like(x)
-    for _ in range(a.apps):
-        lqdd.lq_apply(ctx, a.op, a.prec, x, y)
+    if a.mode == "apply":
+        n = V if a.op == lqdd.LQ_OP_FULL else V // 2
+        x = torch.from_numpy(synth.gaussian_spinor(n, 2003)).cuda()
+        y = torch.empty_like(x)
+        for _ in range(a.apps):
+            lqdd.lq_apply(ctx, a.op, a.prec, x, y)
+        out = float(y.abs().sum())
+    else:
+        b = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()
+        x = torch.zeros_like(b)
+        p = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                             smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+        for _ in range(a.apps):
+            x.zero_()
+            status, st = lqdd.lq_solve(ctx, p, b, x)
+            assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
+        out = st.rel_resid_true
     torch.cuda.synchronize()
-    print("ok", L, "prec", a.prec, "apps", a.apps, float(y.abs().sum()))
+    print("ok", L, a.mode, "prec", a.prec, "apps", a.apps, out)
     lqdd.lq_destroy(ctx)
 
 
