@@ -169,6 +169,25 @@ lq_status lq_smooth(lq_ctx *ctx, const lq_solver_params *params, const void *r, 
 lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, void *x,
                    lq_stats *stats);
 
+/* Solve D x_r = b_r for n_rhs right-hand sides together (1..256), e.g. the 12
+ * spin-colour point sources of a propagator.  Sec. 3.3 names multiple right-hand
+ * sides as the cache-friendly extension: here every operator launch applies D_S
+ * to all right-hand sides, reading each site's links and clover block once.
+ * Method: odd-even reduction (Eq. 2) per right-hand side, then defect correction
+ * in df64 -- R = b_hat - D_S x, stop when ||R_r|| <= tol ||b_hat_r|| for every r --
+ * whose corrections come from batched GMRES(m) in FP32 (Algorithm 2 per right-hand
+ * side, Givens least squares on the device, one CUDA-graph replay per cycle) run to
+ * a relative residual of smooth_tol or smooth_n cycles.
+ *   params->prec must be LQ_DF64, inner_prec LQ_F32; restart = m (1..64);
+ *   max_restarts = outer corrections; smooth_n, smooth_tol as above.
+ *   b, x: n_rhs full spinors back to back ([n_rhs][V][4][3], device); x holds the
+ *   initial guesses on entry.  stats: NULL or n_rhs entries (cycles = iters = outer
+ *   corrections of that right-hand side, inner_iters = inner Arnoldi steps launched
+ *   for it; time, bytes and launches are those of the whole call).  Synchronises.
+ *   LQ_ERR_NOT_CONVERGED still writes every x_r and fills stats. */
+lq_status lq_solve_batch(lq_ctx *ctx, const lq_solver_params *params, int n_rhs, const void *b, void *x,
+                         lq_stats *stats);
+
 /* Copy the clover blocks out for inspection: which = 0 gives C(x), which = 1
  * gives C(x)^{-1} (odd sites only; even entries are zero).  out: device
  * complex double [V][2][6][6], natural site order, block 0 = spins {0,1},

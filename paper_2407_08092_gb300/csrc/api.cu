@@ -60,6 +60,21 @@ struct lq_ctx {
     std::vector<void *> owned;
     std::string err;
     Prof prof;
+    // batched (multi right-hand side) solver state: FP32 workspace, device
+    // Givens state and the captured CUDA graph of one inner GMRES cycle
+    struct Batch {
+        int N = 0, m = 0;
+        void *V = nullptr, *T = nullptr, *X = nullptr, *B = nullptr;
+        BatchRed br{};
+        KState ks{};
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t gexec = nullptr;
+        long long cap_launches = 0;
+        double cap_bytes = 0.0;
+        double *h = nullptr;   // pinned host mirror: est[N] then target[N]
+    } batch;
     Exec ex() { return Exec{g, st, &ctr, &prof}; }
 };
 
@@ -557,6 +572,157 @@ void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
     if (p->smoother == LQ_SMOOTH_GMRES && !(p->smooth_tol >= 0.0)) fail(c, LQ_ERR_ARG, "smooth_tol < 0");
 }
 
+// ---- batched right-hand sides ------------------------------------------------------
+
+// out = D_S in for N consecutive fields: one batched K1 and one batched K2
+// launch, each site's links and clover read once for all right-hand sides
+void op_schur_n(lq_ctx *c, int prec, const void *in, void *out, void *t, int N)
+{
+    Exec e = c->ex();
+    HopCall k1 = hopcall(c, HOP_K1, prec, 1);
+    k1.in = in;
+    k1.out = t;
+    k1.clov = Cip(c, prec);
+    k1.nrhs = N;
+    hop(e, k1);
+    HopCall k2 = hopcall(c, HOP_K2, prec, 0);
+    k2.in = t;
+    k2.in2 = in;
+    k2.out = out;
+    k2.clov = Cp(c, prec, 0);
+    k2.nrhs = N;
+    hop(e, k2);
+}
+
+// FP32 workspace, reduction scratch and device Givens state for N right-hand
+// sides and cycle length m; the captured graph is dropped when they change
+void batch_setup(lq_ctx *c, int N, int m)
+{
+    auto &B = c->batch;
+    if (!B.st) {
+        ck(c, cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(c, cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        ck(c, cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (B.N == N && B.m == m) return;
+    if (B.gexec) cudaGraphExecDestroy(B.gexec);
+    if (B.graph) cudaGraphDestroy(B.graph);
+    B.gexec = nullptr;
+    B.graph = nullptr;
+    if (B.h) cudaFreeHost(B.h);
+    B.h = nullptr;
+    ck(c, cudaMallocHost((void **)&B.h, sizeof(double) * 2 * N), "cudaMallocHost");
+    const size_t f32 = spinor_bytes(c->g, P32);
+    B.V = ws(c, "b:V", (size_t)(m + 1) * N * f32);
+    B.T = ws(c, "b:T", (size_t)N * f32);
+    B.X = ws(c, "b:X", (size_t)N * f32);
+    B.B = ws(c, "b:B", (size_t)N * f32);
+    B.br.blocks = batch_blocks(c->g, N);
+    B.br.pitch = 2 * (2 * m + 2);
+    B.br.partial = (double *)ws(c, "b:part", sizeof(double) * (size_t)N * B.br.blocks * B.br.pitch);
+    B.br.out = (double *)ws(c, "b:out", sizeof(double) * (size_t)N * B.br.pitch);
+    KState &k = B.ks;
+    k.N = N;
+    k.m = m;
+    k.H = (double2 *)ws(c, "b:H", sizeof(double2) * (size_t)N * (m + 1) * m);
+    k.cs = (double *)ws(c, "b:cs", sizeof(double) * (size_t)N * m);
+    k.sn = (double2 *)ws(c, "b:sn", sizeof(double2) * (size_t)N * m);
+    k.g = (double2 *)ws(c, "b:g", sizeof(double2) * (size_t)N * (m + 1));
+    k.y = (double2 *)ws(c, "b:y", sizeof(double2) * (size_t)N * m);
+    k.active = (int *)ws(c, "b:act", sizeof(int) * N);
+    k.kused = (int *)ws(c, "b:ku", sizeof(int) * N);
+    k.nanflag = (int *)ws(c, "b:nan", sizeof(int));
+    k.scale = (double *)ws(c, "b:sc", sizeof(double) * N);
+    k.est = (double *)ws(c, "b:est", sizeof(double) * N);
+    k.target = (double *)ws(c, "b:tg", sizeof(double) * N);
+    B.N = N;
+    B.m = m;
+}
+
+// One cycle of batched GMRES(m) in FP32 on D_S (Algorithm 2 for each right-hand
+// side): r = B - D_S X, Arnoldi with CGS2, Givens on the device, X += V y.
+// A fixed launch sequence without host synchronisation.
+void batch_cycle(lq_ctx *c)
+{
+    auto &B = c->batch;
+    const int N = B.N, m = B.m;
+    Exec e = c->ex();
+    const long long n = 6 * c->g.stride;   // float4 vectors per field
+    const long long vjs = (long long)N * n;
+    const size_t f32 = spinor_bytes(c->g, P32);
+    auto Vj = [&](int j) { return (char *)B.V + (size_t)j * N * f32; };
+    op_schur_n(c, P32, B.X, Vj(0), B.T, N);
+    axpby(e, P32, 1.0, 0.0, B.B, -1.0, 0.0, Vj(0), N);   // V_0 = B - D_S X
+    bnorm(e, P32, Vj(0), N, B.br, 0);
+    bfinish(e, B.br, N, 0, 1);
+    ks_init(e, B.ks, B.br.out, B.br.pitch);
+    bscale(e, Vj(0), B.ks.scale, Vj(0), N);
+    for (int k = 0; k < m; k++) {
+        op_schur_n(c, P32, Vj(k), Vj(k + 1), B.T, N);
+        const int nv = k + 1;
+        bdot(e, B.V, vjs, nv, Vj(k + 1), N, B.br, 0);
+        bfinish(e, B.br, N, 0, nv);
+        baxpy(e, B.V, vjs, nv, B.br.out, B.br.pitch / 2, -1, Vj(k + 1), N, nullptr, 0);
+        bdot(e, B.V, vjs, nv, Vj(k + 1), N, B.br, nv);
+        bfinish(e, B.br, N, nv, nv);
+        baxpy(e, B.V, vjs, nv, B.br.out + 2 * nv, B.br.pitch / 2, -1, Vj(k + 1), N, &B.br, 2 * nv);
+        bfinish(e, B.br, N, 2 * nv, 1);
+        ks_step(e, B.ks, k, B.br.out, B.br.pitch);
+        bscale(e, Vj(k + 1), B.ks.scale, Vj(k + 1), N);
+    }
+    ks_solve(e, B.ks);
+    baxpy(e, B.V, vjs, m, (const double *)B.ks.y, m, +1, B.X, N, nullptr, 0);
+}
+
+// Run one inner cycle: replay the captured graph (captured on first use), or
+// launch eagerly while per-launch profiling is on.
+void batch_run_cycle(lq_ctx *c)
+{
+    auto &B = c->batch;
+    if (c->prof.on) {
+        batch_cycle(c);
+        ck_launch(c, "batched cycle");
+        return;
+    }
+    if (!B.gexec) {
+        const long long l0 = c->ctr.launches;
+        const double b0 = c->ctr.bytes;
+        ck(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        batch_cycle(c);
+        cudaGraph_t graph = nullptr;
+        cudaError_t err = cudaStreamEndCapture(c->st, &graph);
+        ck(c, err, "cudaStreamEndCapture");
+        B.graph = graph;
+        ck(c, cudaGraphInstantiate(&B.gexec, B.graph, 0), "cudaGraphInstantiate");
+        B.cap_launches = c->ctr.launches - l0;
+        B.cap_bytes = c->ctr.bytes - b0;
+        c->ctr.launches = l0;   // counted on each replay instead
+        c->ctr.bytes = b0;
+    }
+    ck(c, cudaGraphLaunch(B.gexec, c->st), "cudaGraphLaunch");
+    c->ctr.launches += B.cap_launches;
+    c->ctr.bytes += B.cap_bytes;
+}
+
+// Runs the batched solve on the context's private stream (capturable), ordered
+// after the caller's stream on entry and before it on exit.
+struct OnBatchStream {
+    lq_ctx *c;
+    cudaStream_t user;
+    explicit OnBatchStream(lq_ctx *c_) : c(c_), user(c_->st)
+    {
+        ck(c, cudaEventRecord(c->batch.ev_in, user), "cudaEventRecord");
+        ck(c, cudaStreamWaitEvent(c->batch.st, c->batch.ev_in, 0), "cudaStreamWaitEvent");
+        c->st = c->batch.st;
+    }
+    ~OnBatchStream()
+    {
+        cudaEventRecord(c->batch.ev_out, c->st);
+        c->st = user;
+        cudaStreamWaitEvent(user, c->batch.ev_out, 0);
+    }
+};
+
 template <typename F>
 lq_status guarded(lq_ctx *c, F &&f)
 {
@@ -646,6 +812,12 @@ lq_status lq_destroy(lq_ctx *c)
         if (p) cudaFree(p);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     for (cudaEvent_t ev : c->prof.pool) cudaEventDestroy(ev);
+    if (c->batch.gexec) cudaGraphExecDestroy(c->batch.gexec);
+    if (c->batch.graph) cudaGraphDestroy(c->batch.graph);
+    if (c->batch.ev_in) cudaEventDestroy(c->batch.ev_in);
+    if (c->batch.ev_out) cudaEventDestroy(c->batch.ev_out);
+    if (c->batch.st) cudaStreamDestroy(c->batch.st);
+    if (c->batch.h) cudaFreeHost(c->batch.h);
     delete c;
     return LQ_OK;
 }
@@ -894,6 +1066,136 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
         st.bytes = c->ctr.bytes - b0;
     }
     if (stats) *stats = st;
+    if (s == LQ_OK && not_conv) {
+        c->err = "tolerance not reached within max_restarts";
+        return LQ_ERR_NOT_CONVERGED;
+    }
+    return s;
+}
+
+lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const void *b, void *x, lq_stats *stats)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = c ? c->ctr.launches : 0;
+    const double by0 = c ? c->ctr.bytes : 0.0;
+    std::vector<lq_stats> st(n_rhs > 0 ? n_rhs : 0);
+    bool not_conv = false;
+    lq_status s = guarded(c, [&] {
+        if (!b || !x || !p || n_rhs < 1 || n_rhs > 256) fail(c, LQ_ERR_ARG, "bad argument");
+        if (p->restart < 1 || p->restart > 64) fail(c, LQ_ERR_ARG, "restart (inner cycle length) out of range 1..64");
+        if (p->max_restarts < 1) fail(c, LQ_ERR_ARG, "max_restarts < 1");
+        if (!(p->tol > 0.0) || !std::isfinite(p->tol)) fail(c, LQ_ERR_ARG, "tol must be positive");
+        if (p->prec != LQ_DF64) fail(c, LQ_ERR_ARG, "the batched outer iteration runs in LQ_DF64");
+        if (p->inner_prec != LQ_F32) fail(c, LQ_ERR_ARG, "the batched inner solver runs in LQ_F32");
+        if (p->smooth_n < 1) fail(c, LQ_ERR_ARG, "smooth_n (inner cycles) < 1");
+        if (!(p->smooth_tol > 0.0 && p->smooth_tol < 1.0)) fail(c, LQ_ERR_ARG, "smooth_tol must be in (0, 1)");
+        need_gauge(c);
+        const int N = n_rhs;
+        batch_setup(c, N, p->restart);
+        auto &B = c->batch;
+        OnBatchStream on(c);
+        Exec e = c->ex();
+        const size_t fw = spinor_bytes(c->g, PDF), f32 = spinor_bytes(c->g, P32);
+        const size_t nat = (size_t)c->g.V * 12 * sizeof(double2);
+        char *BE = (char *)ws(c, "bw:be", N * fw), *BO = (char *)ws(c, "bw:bo", N * fw);
+        char *BH = (char *)ws(c, "bw:bh", N * fw), *XE = (char *)ws(c, "bw:xe", N * fw);
+        char *XO = (char *)ws(c, "bw:xo", N * fw), *R = (char *)ws(c, "bw:r", N * fw);
+        char *T = (char *)ws(c, "bw:t", N * fw), *E = (char *)ws(c, "bw:e", N * fw);
+        // prepare (Eq. 2) every right-hand side
+        for (int r = 0; r < N; r++) {
+            import_full(e, PDF, (const char *)b + r * nat, BE + r * fw, BO + r * fw);
+            import_full(e, PDF, (const char *)x + r * nat, XE + r * fw, XO + r * fw);
+            op_prepare(c, PDF, BE + r * fw, BO + r * fw, BH + r * fw, T);
+        }
+        auto norms = [&](const void *F, std::vector<double> &out) {
+            bnorm(e, PDF, F, N, B.br, 0);
+            bfinish(e, B.br, N, 0, 1);
+            ck(c, cudaMemcpy2DAsync(B.h, sizeof(double), B.br.out, sizeof(double) * B.br.pitch, sizeof(double), N,
+                                    cudaMemcpyDeviceToHost, c->st),
+               "cudaMemcpy2DAsync");
+            sync(c);
+            out.resize(N);
+            for (int r = 0; r < N; r++) out[r] = std::sqrt(B.h[r]);
+        };
+        std::vector<double> bn, rn;
+        norms(BH, bn);
+        std::vector<int> outer(N, 0);
+        std::vector<long long> inner(N, 0);
+        bool all = false;
+        for (int it = 0; it <= p->max_restarts; it++) {
+            // defect: R = b_hat - D_S x in df64
+            op_schur_n(c, PDF, XE, R, T, N);
+            axpby(e, PDF, 1.0, 0.0, BH, -1.0, 0.0, R, N);
+            norms(R, rn);
+            all = true;
+            for (int r = 0; r < N; r++) {
+                if (!std::isfinite(rn[r])) fail(c, LQ_ERR_NAN, "NaN/Inf in a residual");
+                st[r].rel_resid = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+                if (st[r].rel_resid > p->tol) all = false;
+            }
+            if (all || it == p->max_restarts) break;
+            // correction: D_S e = R to smooth_tol (relative) with batched FP32 GMRES
+            for (int r = 0; r < N; r++) convert(e, PDF, R + r * fw, P32, (char *)B.B + r * f32);
+            ck(c, cudaMemsetAsync(B.X, 0, N * f32, c->st), "cudaMemsetAsync");
+            for (int r = 0; r < N; r++) {
+                const bool done = st[r].rel_resid <= p->tol;
+                B.h[N + r] = done ? rn[r] * 2.0 : p->smooth_tol * rn[r];   // converged ones stay idle
+                if (!done) outer[r]++;
+            }
+            ck(c, cudaMemcpyAsync(B.ks.target, B.h + N, sizeof(double) * N, cudaMemcpyHostToDevice, c->st),
+               "cudaMemcpyAsync H2D");
+            ck(c, cudaMemsetAsync(B.ks.nanflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
+            for (int cyc = 0; cyc < p->smooth_n; cyc++) {
+                batch_run_cycle(c);
+                ck(c, cudaMemcpyAsync(B.h, B.ks.est, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st),
+                   "cudaMemcpyAsync D2H");
+                sync(c);
+                bool inner_done = true;
+                for (int r = 0; r < N; r++) {
+                    if (st[r].rel_resid > p->tol) inner[r] += B.m;
+                    if (B.h[r] > B.h[N + r]) inner_done = false;
+                }
+                if (inner_done) break;
+            }
+            int nanflag = 0;
+            ck(c, cudaMemcpy(&nanflag, B.ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+            if (nanflag) fail(c, LQ_ERR_NAN, "NaN/Inf in the batched inner solve");
+            for (int r = 0; r < N; r++) convert(e, P32, (char *)B.X + r * f32, PDF, E + r * fw);
+            axpby(e, PDF, 1.0, 0.0, E, 1.0, 0.0, XE, N);
+        }
+        not_conv = !all;
+        // reconstruct (Eq. 2), export, true residual of every right-hand side
+        void *ye = field(c, PDF, "bw:ye"), *yo = field(c, PDF, "bw:yo");
+        for (int r = 0; r < N; r++) {
+            op_reconstruct(c, PDF, BO + r * fw, XE + r * fw, XO + r * fw);
+            export_full(e, PDF, XE + r * fw, XO + r * fw, (char *)x + r * nat);
+            op_full(c, PDF, XE + r * fw, XO + r * fw, ye, yo);
+            axpby(e, PDF, 1.0, 0.0, BE + r * fw, -1.0, 0.0, ye);
+            axpby(e, PDF, 1.0, 0.0, BO + r * fw, -1.0, 0.0, yo);
+            norm2(e, PDF, ye, c->red, 0);
+            norm2(e, PDF, yo, c->red, 1);
+            norm2(e, PDF, BE + r * fw, c->red, 2);
+            norm2(e, PDF, BO + r * fw, c->red, 3);
+            reduce_finish(e, c->red, 0, 4);
+            const double *hv = fetch(c, 0, 4);
+            const double bb = hv[4] + hv[6];
+            st[r].rel_resid_true = bb > 0 ? std::sqrt((hv[0] + hv[2]) / bb) : 0.0;
+            if (!std::isfinite(st[r].rel_resid_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in a true residual");
+            st[r].cycles = outer[r];
+            st[r].iters = outer[r];
+            st[r].inner_iters = inner[r];
+        }
+        sync(c);
+    });
+    if (c && stats) {
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (int r = 0; r < n_rhs; r++) {
+            st[r].time_ms = ms;
+            st[r].launches = c->ctr.launches - l0;
+            st[r].bytes = c->ctr.bytes - by0;
+            stats[r] = st[r];
+        }
+    }
     if (s == LQ_OK && not_conv) {
         c->err = "tolerance not reached within max_restarts";
         return LQ_ERR_NOT_CONVERGED;

@@ -333,10 +333,11 @@ void copy(const Exec &e, int prec, const void *x, void *y)
     cudaMemcpyAsync(y, x, spinor_bytes(e.g, prec), cudaMemcpyDeviceToDevice, e.st);
 }
 
-void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi, void *y)
+void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi, void *y, int nfields)
 {
-    Launch L_(e, axpy_class(prec), 3.0 * e.g.Vh * sp_bytes(prec), (double)e.g.Vh * 12 * 14);
-    const long long n = nvec(e.g, prec);
+    // nfields consecutive fields are one linear array
+    Launch L_(e, axpy_class(prec), 3.0 * nfields * e.g.Vh * sp_bytes(prec), (double)nfields * e.g.Vh * 12 * 14);
+    const long long n = nvec(e.g, prec) * nfields;
     if (prec == PDF)
         axpby_df_kernel<<<nblk(n), RT, 0, e.st>>>(df64(ar), df64(ai), (const df2 *)x, df64(br), df64(bi), (df2 *)y, n);
     else if (prec == P64)

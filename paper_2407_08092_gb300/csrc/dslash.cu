@@ -118,14 +118,18 @@ struct HopArgs {
     const V *clov;
     R omega;
     int pout;
+    int nrhs;        // right-hand sides sharing the links and clover of this launch
+    long long fs;    // distance between consecutive right-hand sides' fields, in vectors
 };
 
+
 template <typename R, int MODE>
-__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> k)
+__device__ __forceinline__ void hop_body(const Geom &g, const typename St<R>::vec *Uout,
+                                         const typename St<R>::vec *Uin, const typename St<R>::vec *clov, R omega,
+                                         const typename St<R>::vec *in, const typename St<R>::vec *in2,
+                                         const typename St<R>::vec *bv, typename St<R>::vec *out, long long s,
+                                         const Coords &c)
 {
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-    const Coords c = cb_coords(g, s, k.pout);
     const long long st = g.stride;
     cx<R> acc[12];
 #pragma unroll
@@ -138,23 +142,23 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> 
         const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
         const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
         const long long nf = base + (xp >> 1), nb = base + (xm >> 1);
-        hop_dir<0, -1>(acc, k.in, k.Uout, s, nf, st, one);
-        hop_dir<0, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+        hop_dir<0, -1>(acc, in, Uout, s, nf, st, one);
+        hop_dir<0, +1>(acc, in, Uin, nb, nb, st, one);
     }
     // y, z, t: x is unchanged, so the cb index moves by a fixed stride
     {
         const long long d = g.Lxh;
         const long long nf = (c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d;
         const long long nb = (c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d;
-        hop_dir<1, -1>(acc, k.in, k.Uout, s, nf, st, one);
-        hop_dir<1, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+        hop_dir<1, -1>(acc, in, Uout, s, nf, st, one);
+        hop_dir<1, +1>(acc, in, Uin, nb, nb, st, one);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1];
         const long long nf = (c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d;
         const long long nb = (c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d;
-        hop_dir<2, -1>(acc, k.in, k.Uout, s, nf, st, one);
-        hop_dir<2, +1>(acc, k.in, k.Uin, nb, nb, st, one);
+        hop_dir<2, -1>(acc, in, Uout, s, nf, st, one);
+        hop_dir<2, +1>(acc, in, Uin, nb, nb, st, one);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1] * g.L[2];
@@ -162,41 +166,68 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> 
         const long long nf = last ? s - (long long)(g.L[3] - 1) * d : s + d;
         const long long nb = first ? s + (long long)(g.L[3] - 1) * d : s - d;
         const R tb = R(g.tbc);
-        hop_dir<3, -1>(acc, k.in, k.Uout, s, nf, st, last ? tb : one);
-        hop_dir<3, +1>(acc, k.in, k.Uin, nb, nb, st, first ? tb : one);
+        hop_dir<3, -1>(acc, in, Uout, s, nf, st, last ? tb : one);
+        hop_dir<3, +1>(acc, in, Uin, nb, nb, st, first ? tb : one);
     }
 
     cx<R> v[12];
     if (MODE == HOP_K1) {
 #pragma unroll
         for (int i = 0; i < 12; i++) acc[i] = R(-0.5) * acc[i];
-        clover_apply<R>(k.clov, st, s, acc, v);
+        clover_apply<R>(clov, st, s, acc, v);
     } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
         cx<R> x[12];
-        load_spinor_rw(k.in2, st, s, x);
-        clover_apply<R>(k.clov, st, s, x, v);
+        load_spinor_rw(in2, st, s, x);
+        clover_apply<R>(clov, st, s, x, v);
         const R f = MODE == HOP_FULL ? R(-0.5) : R(0.5);
 #pragma unroll
         for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
         if (MODE == HOP_RICH) {
             cx<R> bb[12];
-            load_spinor(k.b, st, s, bb);
+            load_spinor(bv, st, s, bb);
 #pragma unroll
-            for (int i = 0; i < 12; i++) v[i] = x[i] + k.omega * (bb[i] - v[i]);
+            for (int i = 0; i < 12; i++) v[i] = x[i] + omega * (bb[i] - v[i]);
         }
     } else {   // HOP_PREP, HOP_RECON
         cx<R> y[12];
-        load_spinor_rw(k.in2, st, s, y);
+        load_spinor_rw(in2, st, s, y);
 #pragma unroll
         for (int i = 0; i < 12; i++) y[i] = y[i] + R(0.5) * acc[i];
         if (MODE == HOP_RECON) {
-            clover_apply<R>(k.clov, st, s, y, v);
+            clover_apply<R>(clov, st, s, y, v);
         } else {
 #pragma unroll
             for (int i = 0; i < 12; i++) v[i] = y[i];
         }
     }
-    store_spinor(k.out, st, s, v);
+    store_spinor(out, st, s, v);
+}
+
+// One thread per output site.  The batched form (MULTI) loops over the
+// right-hand sides, so each site's links and clover block come from DRAM once
+// and from the caches for the other right-hand sides; it is a separate
+// instantiation so that the single right-hand-side kernel keeps its registers.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(LQ_HOP_THREADS, 3) hop_kernel_multi(Geom g, HopArgs<R> k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+#pragma unroll 1
+    for (int r = 0; r < k.nrhs; r++) {
+        const long long o = r * k.fs;
+        hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in + o, k.in2 ? k.in2 + o : nullptr,
+                          k.b ? k.b + o : nullptr, k.out + o, s, c);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -237,7 +268,8 @@ __device__ __forceinline__ cx<df64> rot_i(cx<df64> z, int q)   // i^q z
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
+__device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &k, const df2 *in, const df2 *in2,
+                                            const df2 *bv, df2 *out, long long s, const Coords &c)
 {
     // per direction d = 2 mu + (backward): the partner of h0 is psi_3 for x, y
     // and psi_2 for z, t (acc_2 takes u_1 resp. u_0); the i-powers
@@ -245,9 +277,6 @@ __global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
     //   qc = {3,1,2,0,3,1,2,0}, qd = {3,1,0,2,1,3,2,0}
     // are packed two bits per direction (no local-memory tables)
     constexpr unsigned QA = 11661u, QB = 10029u, QC = 10023u, QD = 11655u;
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-    const Coords c = cb_coords(g, s, k.pout);
     const long long st = g.stride;
     cx<df64> acc[12];
 #pragma unroll
@@ -272,7 +301,7 @@ __global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
             if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
         }
         cx<df64> p[12];
-        load_spinor(k.in, st, nb, p);
+        load_spinor(in, st, nb, p);
         cx<df64> m[9];
         load_link(fwd ? k.Uout : k.Uin, st, mu, fwd ? s : nb, m);
         const int pa = d < 4 ? 3 : 2;
@@ -320,20 +349,20 @@ __global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
         clover_apply_df(k.clov, st, s, acc, v);
     } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
         cx<df64> x[12];
-        load_spinor_rw(k.in2, st, s, x);
+        load_spinor_rw(in2, st, s, x);
         clover_apply_df(k.clov, st, s, x, v);
         const df64 f = MODE == HOP_FULL ? mhalf : half;
 #pragma unroll
         for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
         if (MODE == HOP_RICH) {
             cx<df64> bb[12];
-            load_spinor(k.b, st, s, bb);
+            load_spinor(bv, st, s, bb);
 #pragma unroll
             for (int i = 0; i < 12; i++) v[i] = x[i] + k.omega * (bb[i] - v[i]);
         }
     } else {
         cx<df64> y[12];
-        load_spinor_rw(k.in2, st, s, y);
+        load_spinor_rw(in2, st, s, y);
 #pragma unroll
         for (int i = 0; i < 12; i++) y[i] = y[i] + half * acc[i];
         if (MODE == HOP_RECON) {
@@ -343,7 +372,21 @@ __global__ void __launch_bounds__(128) hop_df_kernel(Geom g, HopArgs<df64> k)
             for (int i = 0; i < 12; i++) v[i] = y[i];
         }
     }
-    store_spinor(k.out, st, s, v);
+    store_spinor(out, st, s, v);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) hop_df_kernel(const __grid_constant__ Geom g,
+                                                     const __grid_constant__ HopArgs<df64> k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+#pragma unroll 1
+    for (int r = 0; r < k.nrhs; r++) {
+        const long long o = r * k.fs;
+        hop_df_body<MODE>(g, k, k.in + o, k.in2 ? k.in2 + o : nullptr, k.b ? k.b + o : nullptr, k.out + o, s, c);
+    }
 }
 
 template <typename R>
@@ -372,30 +415,34 @@ static void launch_hop(const Exec &e, const HopCall &c)
     k.clov = (const V *)c.clov;
     k.omega = R(c.omega);
     k.pout = c.pout;
+    k.nrhs = c.nrhs;
+    k.fs = (long long)St<R>::SPINOR_VECS * e.g.stride;
     const unsigned blocks = (unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS);
     if constexpr (std::is_same<R, df64>::value)
         hop_df_kernel<MODE><<<blocks, 128, 0, e.st>>>(e.g, k);
+    else if (c.nrhs > 1)
+        hop_kernel_multi<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
     else
         hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
 }
 
 // algorithmic bytes per output site of one hopping launch (FP64 and df64 share
 // the 8-byte-per-real layout)
-static double hop_site_bytes(int mode, int prec)
+static double hop_site_bytes(int mode, int prec, int nrhs)
 {
     const bool wide = prec != P32;
     const double sp = wide ? 192.0 : 96.0;          // spinor
     const double lk = wide ? 144.0 : 48.0;          // link (18 / 12 reals)
     const double cl = wide ? 576.0 : 288.0;         // 72-real clover pair
-    double b = 8 * lk + sp + sp;                    // links, neighbours, output
+    double once = 8 * lk, per = sp + sp;            // links; neighbours and output per rhs
     switch (mode) {
-    case HOP_K1: b += cl; break;
-    case HOP_K2: case HOP_FULL: b += sp + cl; break;
-    case HOP_RICH: b += 2 * sp + cl; break;
-    case HOP_PREP: b += sp; break;
-    case HOP_RECON: b += sp + cl; break;
+    case HOP_K1: once += cl; break;
+    case HOP_K2: case HOP_FULL: once += cl; per += sp; break;
+    case HOP_RICH: once += cl; per += 2 * sp; break;
+    case HOP_PREP: per += sp; break;
+    case HOP_RECON: once += cl; per += sp; break;
     }
-    return b;
+    return once + nrhs * per;
 }
 
 static int hop_class(int mode, int prec)
@@ -418,8 +465,8 @@ void hop(const Exec &e, const HopCall &c)
     // accumulation), 552 per clover-block pair, 24 per spinor add / scale
     static const double hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
                                         1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552};
-    Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec),
-              (double)e.g.Vh * hop_flops[c.mode]);
+    Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec, c.nrhs),
+              (double)e.g.Vh * hop_flops[c.mode] * c.nrhs);
     switch (c.mode) {
         LQ_CASE(HOP_K1)
         LQ_CASE(HOP_K2)

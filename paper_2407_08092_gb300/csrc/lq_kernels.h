@@ -126,6 +126,7 @@ struct HopCall {
     const void *U[2];      // link copies of both parities (this precision)
     const void *clov;      // C or C^{-1} of the output parity (this precision)
     double omega;          // HOP_RICH weight
+    int nrhs = 1;          // right-hand sides: in, in2, b, out are nrhs consecutive fields
 };
 void hop(const Exec &e, const HopCall &c);
 // out = C in (site-diagonal apply of packed blocks of one parity)
@@ -138,7 +139,7 @@ void zero(const Exec &e, int prec, void *x);
 void copy(const Exec &e, int prec, const void *x, void *y);
 // y = a x + b y  (complex a, b; host scalars)
 void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi,
-           void *y);
+           void *y, int nfields = 1);
 // Reduction scratch: per-block partials and the finished values, in device
 // memory owned by the context.  Slot i holds a complex value at [2i, 2i+1].
 struct RedScratch {
@@ -162,5 +163,41 @@ void reduce_finish(const Exec &e, const RedScratch &r, int first, int count);
 // norm of a natural c128 field of n sites (used by lq_norm2)
 void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch &r, int slot);
 int reduction_blocks(const Geom &g);
+
+// ---- batched right-hand sides (batch.cu) -------------------------------------
+// Reduction scratch of a batch: partial[N][blocks][pitch], out[N][pitch]
+// (doubles; complex slot i at [2i, 2i+1] of a right-hand side's row).
+struct BatchRed {
+    double *partial;
+    double *out;
+    int blocks;
+    int pitch;
+};
+// Device-side Givens state of the batched GMRES: N right-hand sides, cycle m.
+struct KState {
+    int N, m;
+    double2 *H;       // [N][m][m+1] Hessenberg columns (rotated in place)
+    double *cs;       // [N][m]
+    double2 *sn;      // [N][m]
+    double2 *g;       // [N][m+1]
+    double2 *y;       // [N][m] least-squares solution
+    int *active;      // [N] cycle continues for this right-hand side
+    int *kused;       // [N] Arnoldi steps taken this cycle
+    int *nanflag;     // NaN/Inf seen
+    double *scale;    // [N] normaliser of the newest basis vector (0 when inactive)
+    double *est;      // [N] residual estimate |g_{k+1}|
+    double *target;   // [N] absolute residual target of the cycle
+};
+// FP32 batched BLAS; basis vector j of right-hand side r at V + j * vjs + r * n vectors
+void bdot(const Exec &e, const void *V, long long vjs, int nv, const void *w, int N, BatchRed &br, int slot0);
+void baxpy(const Exec &e, const void *V, long long vjs, int nv, const double *c, int cstride, int sign, void *y,
+           int N, BatchRed *br, int slot);
+void bnorm(const Exec &e, int prec, const void *w, int N, BatchRed &br, int slot);   // P32 or PDF
+void bfinish(const Exec &e, BatchRed &br, int N, int first, int count);
+void bscale(const Exec &e, const void *x, const double *s, void *y, int N);
+void ks_init(const Exec &e, const KState &k, const double *nrm2, int nstride);
+void ks_step(const Exec &e, const KState &k, int step, const double *dots, int dstride);
+void ks_solve(const Exec &e, const KState &k);
+int batch_blocks(const Geom &g, int N);
 
 }  // namespace lq

@@ -194,6 +194,29 @@ def lq_solve(ctx, params: lq_solver_params, b, x):
     return s, st
 
 
+_lib.lq_solve_batch.argtypes = [_P, ctypes.POINTER(lq_solver_params), ctypes.c_int, _P, _P,
+                                ctypes.POINTER(lq_stats)]
+_lib.lq_solve_batch.restype = ctypes.c_int
+
+
+def lq_solve_batch(ctx, params: lq_solver_params, n_rhs: int, b, x):
+    """Batched solve of n_rhs systems; b, x are [n_rhs, V, 4, 3] complex128 CUDA
+    tensors.  Returns (status, [stats per right-hand side]); raises on every
+    status but OK and NOT_CONVERGED."""
+    st = (lq_stats * int(n_rhs))()
+    s = _lib.lq_solve_batch(ctx, ctypes.byref(params), int(n_rhs), _ptr(b), _ptr(x), st)
+    if s not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctx, s)
+    return s, list(st)
+
+
+def make_batch_params(tol=1e-10, restart=16, max_restarts=10, smooth_n=8, smooth_tol=1e-5) -> lq_solver_params:
+    """Parameters of lq_solve_batch: df64 defect correction around batched FP32 GMRES(restart)."""
+    return make_params(solver=LQ_SOLVER_GMRES, prec=LQ_DF64, tol=tol, restart=restart, max_restarts=max_restarts,
+                       smoother=LQ_SMOOTH_GMRES, smooth_n=smooth_n, smooth_m=restart, smooth_tol=smooth_tol,
+                       inner_prec=LQ_F32)
+
+
 def lq_export_clover(ctx, which: int, out) -> None:
     _check(ctx, _lib.lq_export_clover(ctx, int(which), _ptr(out)))
 
