@@ -69,11 +69,12 @@ struct lq_ctx {
         KState ks{};
         cudaStream_t st = nullptr;
         cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t gexec = nullptr;
-        long long cap_launches = 0;
-        double cap_bytes = 0.0;
+        // captured segments of a cycle: [0] start, [1..nseg] Arnoldi steps, [nseg+1] finish
+        std::vector<cudaGraphExec_t> gexec;
+        std::vector<long long> cap_launches;
+        std::vector<double> cap_bytes;
         double *h = nullptr;   // pinned host mirror: est[N] then target[N]
+        int *hact = nullptr;   // pinned host mirror of the active flags
     } batch;
     Exec ex() { return Exec{g, st, &ctr, &prof}; }
 };
@@ -354,10 +355,26 @@ void upload_coef(lq_ctx *c, const std::vector<cd> &y)
 
 // Arnoldi step: w <- w orthogonalised against V[0..k] by CGS2; returns the
 // Hessenberg column h[0..k] and h_{k+1,k} = ||w|| (not yet normalised)
+// The FP64-class solvers orthogonalise twice (CGS2); the FP32 solvers, which
+// only ever serve as preconditioners or smoothers under an FP64-class outer
+// iteration, orthogonalise once (classical Gram-Schmidt: one multi-dot and one
+// multi-axpy with the new norm fused), half the basis sweeps of CGS2.
 double arnoldi_cgs2(lq_ctx *c, int prec, void *V, int k, void *w, Hess &H)
 {
     Exec e = c->ex();
     const int n = k + 1;
+    if (prec == P32) {
+        multi_dot(e, prec, V, n, w, c->red, 0);
+        reduce_finish(e, c->red, 0, n);
+        multi_axpy(e, prec, V, n, c->red.out, -1, w, &c->red, n);
+        reduce_finish(e, c->red, n, 1);
+        ck_launch(c, "arnoldi");
+        const double *hv = fetch(c, 0, n + 1);
+        for (int j = 0; j < n; j++) H.h(j, k) = cd(hv[2 * j], hv[2 * j + 1]);
+        const double nrm2 = hv[2 * n];
+        if (!std::isfinite(nrm2)) fail(c, LQ_ERR_NAN, "NaN/Inf in the Arnoldi process");
+        return std::sqrt(nrm2);
+    }
     multi_dot(e, prec, V, n, w, c->red, 0);
     reduce_finish(e, c->red, 0, n);
     multi_axpy(e, prec, V, n, c->red.out, -1, w, nullptr, 0);
@@ -605,13 +622,17 @@ void batch_setup(lq_ctx *c, int N, int m)
         ck(c, cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming), "cudaEventCreate");
     }
     if (B.N == N && B.m == m) return;
-    if (B.gexec) cudaGraphExecDestroy(B.gexec);
-    if (B.graph) cudaGraphDestroy(B.graph);
-    B.gexec = nullptr;
-    B.graph = nullptr;
+    for (cudaGraphExec_t g : B.gexec)
+        if (g) cudaGraphExecDestroy(g);
+    B.gexec.clear();
+    B.cap_launches.clear();
+    B.cap_bytes.clear();
     if (B.h) cudaFreeHost(B.h);
+    if (B.hact) cudaFreeHost(B.hact);
     B.h = nullptr;
+    B.hact = nullptr;
     ck(c, cudaMallocHost((void **)&B.h, sizeof(double) * 2 * N), "cudaMallocHost");
+    ck(c, cudaMallocHost((void **)&B.hact, sizeof(int) * N), "cudaMallocHost");
     const size_t f32 = spinor_bytes(c->g, P32);
     B.V = ws(c, "b:V", (size_t)(m + 1) * N * f32);
     B.T = ws(c, "b:T", (size_t)N * f32);
@@ -640,68 +661,120 @@ void batch_setup(lq_ctx *c, int N, int m)
 }
 
 // One cycle of batched GMRES(m) in FP32 on D_S (Algorithm 2 for each right-hand
-// side): r = B - D_S X, Arnoldi with CGS2, Givens on the device, X += V y.
-// A fixed launch sequence without host synchronisation.
-void batch_cycle(lq_ctx *c)
+// side), in three kinds of segment, each a fixed launch sequence without host
+// synchronisation:
+//   start:  r = B - D_S X, beta = ||r||, g = beta e_1, V_0 = r / beta
+//   steps:  Arnoldi steps [k0, k1): w = D_S v_k, CGS2, Givens on the device, v_{k+1}
+//   finish: y = R^{-1} g, X += V y
+static constexpr int BATCH_SEG = 4;   // Arnoldi steps per segment
+
+void batch_start(lq_ctx *c)
 {
     auto &B = c->batch;
-    const int N = B.N, m = B.m;
+    const int N = B.N;
     Exec e = c->ex();
-    const long long n = 6 * c->g.stride;   // float4 vectors per field
-    const long long vjs = (long long)N * n;
-    const size_t f32 = spinor_bytes(c->g, P32);
-    auto Vj = [&](int j) { return (char *)B.V + (size_t)j * N * f32; };
-    op_schur_n(c, P32, B.X, Vj(0), B.T, N);
-    axpby(e, P32, 1.0, 0.0, B.B, -1.0, 0.0, Vj(0), N);   // V_0 = B - D_S X
-    bnorm(e, P32, Vj(0), N, B.br, 0);
+    op_schur_n(c, P32, B.X, B.V, B.T, N);
+    axpby(e, P32, 1.0, 0.0, B.B, -1.0, 0.0, B.V, N);   // V_0 = B - D_S X
+    bnorm(e, P32, B.V, N, B.br, 0);
     bfinish(e, B.br, N, 0, 1);
     ks_init(e, B.ks, B.br.out, B.br.pitch);
-    bscale(e, Vj(0), B.ks.scale, Vj(0), N);
-    for (int k = 0; k < m; k++) {
+    bscale(e, B.V, B.ks.scale, B.V, N);
+}
+
+void batch_steps(lq_ctx *c, int k0, int k1)
+{
+    auto &B = c->batch;
+    const int N = B.N;
+    Exec e = c->ex();
+    const long long vjs = (long long)N * 6 * c->g.stride;   // float4 vectors between basis vectors
+    const size_t f32 = spinor_bytes(c->g, P32);
+    auto Vj = [&](int j) { return (char *)B.V + (size_t)j * N * f32; };
+    for (int k = k0; k < k1; k++) {
         op_schur_n(c, P32, Vj(k), Vj(k + 1), B.T, N);
+        // one classical Gram-Schmidt pass with the new norm fused (FP32 inner solver)
         const int nv = k + 1;
         bdot(e, B.V, vjs, nv, Vj(k + 1), N, B.br, 0);
         bfinish(e, B.br, N, 0, nv);
-        baxpy(e, B.V, vjs, nv, B.br.out, B.br.pitch / 2, -1, Vj(k + 1), N, nullptr, 0);
-        bdot(e, B.V, vjs, nv, Vj(k + 1), N, B.br, nv);
-        bfinish(e, B.br, N, nv, nv);
-        baxpy(e, B.V, vjs, nv, B.br.out + 2 * nv, B.br.pitch / 2, -1, Vj(k + 1), N, &B.br, 2 * nv);
-        bfinish(e, B.br, N, 2 * nv, 1);
-        ks_step(e, B.ks, k, B.br.out, B.br.pitch);
+        baxpy(e, B.V, vjs, nv, B.br.out, B.br.pitch / 2, -1, Vj(k + 1), N, &B.br, nv);
+        bfinish(e, B.br, N, nv, 1);
+        ks_step(e, B.ks, k, 1, B.br.out, B.br.pitch);
         bscale(e, Vj(k + 1), B.ks.scale, Vj(k + 1), N);
     }
-    ks_solve(e, B.ks);
-    baxpy(e, B.V, vjs, m, (const double *)B.ks.y, m, +1, B.X, N, nullptr, 0);
 }
 
-// Run one inner cycle: replay the captured graph (captured on first use), or
-// launch eagerly while per-launch profiling is on.
-void batch_run_cycle(lq_ctx *c)
+void batch_finish(lq_ctx *c)
 {
     auto &B = c->batch;
+    Exec e = c->ex();
+    const long long vjs = (long long)B.N * 6 * c->g.stride;
+    ks_solve(e, B.ks);
+    baxpy(e, B.V, vjs, B.m, (const double *)B.ks.y, B.m, +1, B.X, B.N, nullptr, 0);
+}
+
+// Segment `id` (0 start, 1..nseg steps, nseg+1 finish): replayed from its CUDA
+// graph, captured on first use; launched eagerly while per-launch profiling is
+// on.  Launches and bytes are counted on every replay.
+void batch_segment(lq_ctx *c, int id)
+{
+    auto &B = c->batch;
+    const int nseg = (B.m + BATCH_SEG - 1) / BATCH_SEG;
+    auto body = [&]() {
+        if (id == 0) batch_start(c);
+        else if (id <= nseg) batch_steps(c, (id - 1) * BATCH_SEG, std::min(B.m, id * BATCH_SEG));
+        else batch_finish(c);
+    };
     if (c->prof.on) {
-        batch_cycle(c);
-        ck_launch(c, "batched cycle");
+        body();
+        ck_launch(c, "batched segment");
         return;
     }
-    if (!B.gexec) {
+    if ((int)B.gexec.size() < nseg + 2) {
+        B.gexec.resize(nseg + 2, nullptr);
+        B.cap_launches.resize(nseg + 2, 0);
+        B.cap_bytes.resize(nseg + 2, 0.0);
+    }
+    if (!B.gexec[id]) {
         const long long l0 = c->ctr.launches;
         const double b0 = c->ctr.bytes;
         ck(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-        batch_cycle(c);
+        body();
         cudaGraph_t graph = nullptr;
-        cudaError_t err = cudaStreamEndCapture(c->st, &graph);
+        const cudaError_t err = cudaStreamEndCapture(c->st, &graph);
         ck(c, err, "cudaStreamEndCapture");
-        B.graph = graph;
-        ck(c, cudaGraphInstantiate(&B.gexec, B.graph, 0), "cudaGraphInstantiate");
-        B.cap_launches = c->ctr.launches - l0;
-        B.cap_bytes = c->ctr.bytes - b0;
-        c->ctr.launches = l0;   // counted on each replay instead
+        const cudaError_t ierr = cudaGraphInstantiate(&B.gexec[id], graph, 0);
+        cudaGraphDestroy(graph);
+        ck(c, ierr, "cudaGraphInstantiate");
+        B.cap_launches[id] = c->ctr.launches - l0;
+        B.cap_bytes[id] = c->ctr.bytes - b0;
+        c->ctr.launches = l0;
         c->ctr.bytes = b0;
     }
-    ck(c, cudaGraphLaunch(B.gexec, c->st), "cudaGraphLaunch");
-    c->ctr.launches += B.cap_launches;
-    c->ctr.bytes += B.cap_bytes;
+    ck(c, cudaGraphLaunch(B.gexec[id], c->st), "cudaGraphLaunch");
+    c->ctr.launches += B.cap_launches[id];
+    c->ctr.bytes += B.cap_bytes[id];
+}
+
+// One inner cycle: start, step segments until every right-hand side has left
+// the cycle (host check of the active flags between segments), finish.
+// Returns the Arnoldi steps launched.
+int batch_run_cycle(lq_ctx *c)
+{
+    auto &B = c->batch;
+    const int nseg = (B.m + BATCH_SEG - 1) / BATCH_SEG;
+    batch_segment(c, 0);
+    int steps = 0;
+    for (int j = 1; j <= nseg; j++) {
+        ck(c, cudaMemcpyAsync(B.hact, B.ks.active, sizeof(int) * B.N, cudaMemcpyDeviceToHost, c->st),
+           "cudaMemcpyAsync D2H");
+        sync(c);
+        bool any = false;
+        for (int r = 0; r < B.N; r++) any = any || B.hact[r];
+        if (!any) break;
+        batch_segment(c, j);
+        steps += std::min(B.m, j * BATCH_SEG) - (j - 1) * BATCH_SEG;
+    }
+    batch_segment(c, nseg + 1);
+    return steps;
 }
 
 // Runs the batched solve on the context's private stream (capturable), ordered
@@ -812,8 +885,9 @@ lq_status lq_destroy(lq_ctx *c)
         if (p) cudaFree(p);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     for (cudaEvent_t ev : c->prof.pool) cudaEventDestroy(ev);
-    if (c->batch.gexec) cudaGraphExecDestroy(c->batch.gexec);
-    if (c->batch.graph) cudaGraphDestroy(c->batch.graph);
+    for (cudaGraphExec_t g : c->batch.gexec)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->batch.hact) cudaFreeHost(c->batch.hact);
     if (c->batch.ev_in) cudaEventDestroy(c->batch.ev_in);
     if (c->batch.ev_out) cudaEventDestroy(c->batch.ev_out);
     if (c->batch.st) cudaStreamDestroy(c->batch.st);
@@ -1146,19 +1220,22 @@ lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const 
                "cudaMemcpyAsync H2D");
             ck(c, cudaMemsetAsync(B.ks.nanflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
             for (int cyc = 0; cyc < p->smooth_n; cyc++) {
-                batch_run_cycle(c);
+                const int steps = batch_run_cycle(c);
                 ck(c, cudaMemcpyAsync(B.h, B.ks.est, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st),
                    "cudaMemcpyAsync D2H");
                 sync(c);
                 bool inner_done = true;
                 for (int r = 0; r < N; r++) {
-                    if (st[r].rel_resid > p->tol) inner[r] += B.m;
+                    if (st[r].rel_resid > p->tol) inner[r] += steps;
                     if (B.h[r] > B.h[N + r]) inner_done = false;
                 }
                 if (inner_done) break;
             }
             int nanflag = 0;
-            ck(c, cudaMemcpy(&nanflag, B.ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+            ck(c, cudaMemcpyAsync(&B.hact[0], B.ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+               "cudaMemcpyAsync D2H");
+            sync(c);
+            nanflag = B.hact[0];
             if (nanflag) fail(c, LQ_ERR_NAN, "NaN/Inf in the batched inner solve");
             for (int r = 0; r < N; r++) convert(e, P32, (char *)B.X + r * f32, PDF, E + r * fw);
             axpby(e, PDF, 1.0, 0.0, E, 1.0, 0.0, XE, N);

@@ -234,12 +234,14 @@ __global__ void ks_init_kernel(int N, int m, const double *nrm2, int nstride, co
     est[r] = beta;
 }
 
-// After Arnoldi step k: h_jk = h1_j + h2_j (j <= k) from slots [0, k] and
-// [k+1, 2k+1], ||w||^2 in slot 2k+2 of each right-hand side's row of `dots`.
+// After Arnoldi step k.  Two orthogonalisation passes (CGS2): h_jk = h1_j + h2_j
+// (j <= k) from slots [0, k] and [k+1, 2k+1], ||w||^2 in slot 2k+2 of each
+// right-hand side's row of `dots`; one pass (CGS): h_jk from slots [0, k] and
+// ||w||^2 in slot k+1.
 // Rotates the new Hessenberg column, updates g, and decides whether the cycle
 // continues for this right-hand side (residual estimate above target, no
 // breakdown).  scale_r = 1/h_{k+1,k} normalises the next basis vector.
-__global__ void ks_step_kernel(int N, int m, int k, const double *dots, int dstride, const double *target,
+__global__ void ks_step_kernel(int N, int m, int k, int passes, const double *dots, int dstride, const double *target,
                                double2 *H, double *cs, double2 *sn, double2 *g, int *active, int *kused,
                                double *scale, double *est, int *nanflag)
 {
@@ -254,10 +256,11 @@ __global__ void ks_step_kernel(int N, int m, int k, const double *dots, int dstr
     double *csr = cs + (long long)r * m;
     double2 *snr = sn + (long long)r * m;
     double2 *gr = g + (long long)r * (m + 1);
-    const double hk1 = sqrt(d[2 * (2 * k + 2)]);
+    const double hk1 = sqrt(d[2 * (passes == 2 ? 2 * k + 2 : k + 1)]);
     double colnorm2 = hk1 * hk1;
     for (int j = 0; j <= k; j++) {
-        const double re = d[2 * j] + d[2 * (k + 1 + j)], im = d[2 * j + 1] + d[2 * (k + 1 + j) + 1];
+        const double re = d[2 * j] + (passes == 2 ? d[2 * (k + 1 + j)] : 0.0);
+        const double im = d[2 * j + 1] + (passes == 2 ? d[2 * (k + 1 + j) + 1] : 0.0);
         Hr[(long long)k * (m + 1) + j] = make_double2(re, im);
         colnorm2 += re * re + im * im;
     }
@@ -413,10 +416,10 @@ void ks_init(const Exec &e, const KState &k, const double *nrm2, int nstride)
                                                      k.scale, k.est);
 }
 
-void ks_step(const Exec &e, const KState &k, int step, const double *dots, int dstride)
+void ks_step(const Exec &e, const KState &k, int step, int passes, const double *dots, int dstride)
 {
     Launch L_(e, K_FINISH, 0.0);
-    ks_step_kernel<<<(k.N + 31) / 32, 32, 0, e.st>>>(k.N, k.m, step, dots, dstride, k.target, k.H, k.cs, k.sn, k.g,
+    ks_step_kernel<<<(k.N + 31) / 32, 32, 0, e.st>>>(k.N, k.m, step, passes, dots, dstride, k.target, k.H, k.cs, k.sn, k.g,
                                                      k.active, k.kused, k.scale, k.est, k.nanflag);
 }
 

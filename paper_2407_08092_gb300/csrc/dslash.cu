@@ -217,17 +217,20 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> 
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(LQ_HOP_THREADS, 3) hop_kernel_multi(Geom g, HopArgs<R> k)
+__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel_multi(Geom g, HopArgs<R> k)
 {
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
+    // block = 32 consecutive sites (x) for MRHS_PER_BLOCK right-hand sides (y);
+    // consecutive blocks cover the right-hand-side groups of the same sites, so
+    // a site's links and clover block reach L1/L2 once for all of them
+    const int groups = (k.nrhs + blockDim.y - 1) / blockDim.y;
+    const long long sb = blockIdx.x / groups;
+    const int r = (blockIdx.x - sb * groups) * blockDim.y + threadIdx.y;
+    const long long s = sb * 32 + threadIdx.x;
+    if (s >= g.Vh || r >= k.nrhs) return;
     const Coords c = cb_coords(g, s, k.pout);
-#pragma unroll 1
-    for (int r = 0; r < k.nrhs; r++) {
-        const long long o = r * k.fs;
-        hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in + o, k.in2 ? k.in2 + o : nullptr,
-                          k.b ? k.b + o : nullptr, k.out + o, s, c);
-    }
+    const long long o = r * k.fs;
+    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in + o, k.in2 ? k.in2 + o : nullptr,
+                      k.b ? k.b + o : nullptr, k.out + o, s, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -421,7 +424,11 @@ static void launch_hop(const Exec &e, const HopCall &c)
     if constexpr (std::is_same<R, df64>::value)
         hop_df_kernel<MODE><<<blocks, 128, 0, e.st>>>(e.g, k);
     else if (c.nrhs > 1)
-        hop_kernel_multi<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+    {
+        const int rpb = LQ_HOP_THREADS / 32;   // right-hand sides per block
+        const long long sblocks = (e.g.Vh + 31) / 32, groups = (c.nrhs + rpb - 1) / rpb;
+        hop_kernel_multi<R, MODE><<<(unsigned)(sblocks * groups), dim3(32, rpb), 0, e.st>>>(e.g, k);
+    }
     else
         hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
 }

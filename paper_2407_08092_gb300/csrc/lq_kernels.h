@@ -196,7 +196,7 @@ void bnorm(const Exec &e, int prec, const void *w, int N, BatchRed &br, int slot
 void bfinish(const Exec &e, BatchRed &br, int N, int first, int count);
 void bscale(const Exec &e, const void *x, const double *s, void *y, int N);
 void ks_init(const Exec &e, const KState &k, const double *nrm2, int nstride);
-void ks_step(const Exec &e, const KState &k, int step, const double *dots, int dstride);
+void ks_step(const Exec &e, const KState &k, int step, int passes, const double *dots, int dstride);
 void ks_solve(const Exec &e, const KState &k);
 int batch_blocks(const Geom &g, int N);
 

@@ -21,7 +21,8 @@ def main():
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32, 2 df64")
     ap.add_argument("--apps", type=int, default=3)
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch"])
+    ap.add_argument("--nrhs", type=int, default=12)
     a = ap.parse_args()
     L = tuple(int(v) for v in a.lattice.split(","))
     V = int(np.prod(L))
@@ -34,6 +35,19 @@ def main():
         for _ in range(a.apps):
             lqdd.lq_apply(ctx, a.op, a.prec, x, y)
         out = float(y.abs().sum())
+    elif a.mode == "batch":
+        n = a.nrhs
+        b = torch.zeros((n, V, 4, 3), dtype=torch.complex128, device="cuda")
+        for r in range(n):
+            b[r, 0, r % 4, (r // 4) % 3] = 1.0
+        x = torch.zeros_like(b)
+        for _ in range(a.apps):
+            x.zero_()
+            status, st = lqdd.lq_solve_batch(ctx, lqdd.make_batch_params(), n, b, x)
+            assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
+        out = max(s.rel_resid_true for s in st)
+        print("outer corrections", [s.iters for s in st], "inner steps", [s.inner_iters for s in st],
+              "ms", round(st[0].time_ms, 2))
     else:
         b = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()
         x = torch.zeros_like(b)
