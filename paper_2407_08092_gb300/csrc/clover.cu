@@ -26,54 +26,6 @@ struct M3 {
     cx<R> a[9];
 };
 
-// C = A B, A^+ B, A B^+ (kept out of line: in df64 each is ~1.6k instructions,
-// and one copy per call site would overflow the instruction cache)
-template <typename R>
-__device__ __noinline__ M3<R> mm(const M3<R> &A, const M3<R> &B)
-{
-    M3<R> C;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<R> acc = cmul(A.a[i * 3], B.a[j]);
-            acc = cfma(A.a[i * 3 + 1], B.a[3 + j], acc);
-            acc = cfma(A.a[i * 3 + 2], B.a[6 + j], acc);
-            C.a[i * 3 + j] = acc;
-        }
-    return C;
-}
-template <typename R>
-__device__ __noinline__ M3<R> mdm(const M3<R> &A, const M3<R> &B)
-{
-    M3<R> C;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<R> acc = cmulc(A.a[i], B.a[j]);
-            acc = cfmac(A.a[3 + i], B.a[3 + j], acc);
-            acc = cfmac(A.a[6 + i], B.a[6 + j], acc);
-            C.a[i * 3 + j] = acc;
-        }
-    return C;
-}
-template <typename R>
-__device__ __noinline__ M3<R> mmd(const M3<R> &A, const M3<R> &B)
-{
-    M3<R> C;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<R> acc = cmul(A.a[i * 3], cconj(B.a[j * 3]));
-            acc = cfma(A.a[i * 3 + 1], cconj(B.a[j * 3 + 1]), acc);
-            acc = cfma(A.a[i * 3 + 2], cconj(B.a[j * 3 + 2]), acc);
-            C.a[i * 3 + j] = acc;
-        }
-    return C;
-}
-
 // the link U_mu at coordinates c, read from the internal per-parity copies
 template <typename R>
 __device__ __forceinline__ M3<R> link_at(const Geom &g, const typename St<R>::vec *Ue,
@@ -84,59 +36,6 @@ __device__ __forceinline__ M3<R> link_at(const Geom &g, const typename St<R>::ve
     M3<R> m;
     load_link(parity ? Uo : Ue, g.stride, mu, lex >> 1, m.a);
     return m;
-}
-
-__device__ __forceinline__ void shifted(const Geom &g, const int c0[4], int mu, int dmu, int nu, int dnu, int c[4])
-{
-    c[0] = c0[0];
-    c[1] = c0[1];
-    c[2] = c0[2];
-    c[3] = c0[3];
-    c[mu] = (c[mu] + dmu + g.L[mu]) % g.L[mu];
-    c[nu] = (c[nu] + dnu + g.L[nu]) % g.L[nu];
-}
-
-// F = (Q - Q^+)/8 for the plane (mu, nu) at site c; Q = the four leaves
-template <typename R>
-__device__ void field_strength(const Geom &g, const typename St<R>::vec *Ue, const typename St<R>::vec *Uo,
-                               const int c[4], int mu, int nu, M3<R> &F)
-{
-    int xpm[4], xpn[4], xmm[4], xmn[4], xmmpn[4], xmmmn[4], xpmmn[4];
-    shifted(g, c, mu, 1, nu, 0, xpm);
-    shifted(g, c, mu, 0, nu, 1, xpn);
-    shifted(g, c, mu, -1, nu, 0, xmm);
-    shifted(g, c, mu, 0, nu, -1, xmn);
-    shifted(g, c, mu, -1, nu, 1, xmmpn);
-    shifted(g, c, mu, -1, nu, -1, xmmmn);
-    shifted(g, c, mu, 1, nu, -1, xpmmn);
-    M3<R> Q, T;
-    // +mu +nu -mu -nu
-    T = mm(link_at<R>(g, Ue, Uo, c, mu), link_at<R>(g, Ue, Uo, xpm, nu));
-    T = mmd(T, link_at<R>(g, Ue, Uo, xpn, mu));
-    Q = mmd(T, link_at<R>(g, Ue, Uo, c, nu));
-    // +nu -mu -nu +mu
-    T = mmd(link_at<R>(g, Ue, Uo, c, nu), link_at<R>(g, Ue, Uo, xmmpn, mu));
-    T = mmd(T, link_at<R>(g, Ue, Uo, xmm, nu));
-    T = mm(T, link_at<R>(g, Ue, Uo, xmm, mu));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
-    // -mu -nu +mu +nu:  U_mu(x-mu)^+ U_nu(x-mu-nu)^+ = (U_nu(x-mu-nu) U_mu(x-mu))^+
-    T = mm(link_at<R>(g, Ue, Uo, xmmmn, nu), link_at<R>(g, Ue, Uo, xmm, mu));
-    T = mdm(T, link_at<R>(g, Ue, Uo, xmmmn, mu));
-    T = mm(T, link_at<R>(g, Ue, Uo, xmn, nu));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
-    // -nu +mu +nu -mu
-    T = mdm(link_at<R>(g, Ue, Uo, xmn, nu), link_at<R>(g, Ue, Uo, xmn, mu));
-    T = mm(T, link_at<R>(g, Ue, Uo, xpmmn, nu));
-    T = mmd(T, link_at<R>(g, Ue, Uo, c, mu));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
-    const R eighth = R(0.125);
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) F.a[i * 3 + j] = eighth * (Q.a[i * 3 + j] - cconj(Q.a[j * 3 + i]));
 }
 
 __device__ __forceinline__ void store_pair(double2 *p, double a, double b) { *p = make_double2(a, b); }
@@ -150,9 +49,22 @@ __device__ __forceinline__ bool positive(df64 d) { return df_positive(d); }
 __constant__ int c_pmu[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int c_pnu[6] = {1, 2, 2, 3, 3, 3};
 
-template <typename R>
-__global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const typename St<R>::vec *__restrict__ Ue,
-                                                           const typename St<R>::vec *__restrict__ Uo, float2 *Fb)
+// The 16 link factors of the four leaves of plane (mu, nu), leaf by leaf:
+//   leaf 1: U_mu(x)       U_nu(x+mu)        U_mu(x+nu)^+     U_nu(x)^+
+//   leaf 2: U_nu(x)       U_mu(x-mu+nu)^+   U_nu(x-mu)^+     U_mu(x-mu)
+//   leaf 3: U_mu(x-mu)^+  U_nu(x-mu-nu)^+   U_mu(x-mu-nu)    U_nu(x-nu)
+//   leaf 4: U_nu(x-nu)^+  U_mu(x-nu)        U_nu(x+mu-nu)    U_mu(x)^+
+// as the site offset along mu and nu, whether the link points along nu, and
+// whether it enters as U^+.  Walking this table lets one inlined 3x3 product
+// serve all twelve products (the df64 code stays small enough for the
+// instruction cache).
+__constant__ signed char c_ldmu[16] = {0, 1, 0, 0, 0, -1, -1, -1, -1, -1, -1, 0, 0, 0, 1, 0};
+__constant__ signed char c_ldnu[16] = {0, 0, 1, 0, 0, 1, 0, 0, 0, -1, -1, -1, -1, -1, -1, 0};
+__constant__ unsigned char c_lnu[16] = {0, 1, 0, 1, 1, 0, 1, 0, 0, 1, 0, 1, 1, 0, 1, 0};
+__constant__ unsigned char c_ldag[16] = {0, 0, 1, 1, 0, 1, 1, 0, 1, 1, 0, 0, 1, 0, 0, 1};
+
+__global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const df2 *__restrict__ Ue,
+                                                           const df2 *__restrict__ Uo, float2 *Fb)
 {
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 6 * g.V) return;
@@ -165,9 +77,52 @@ __global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const typenam
         c[1] = (int)(r % g.L[1]); r /= g.L[1];
         c[2] = (int)(r % g.L[2]); c[3] = (int)(r / g.L[2]);
     }
-    M3<R> F;
-    field_strength<R>(g, Ue, Uo, c, c_pmu[p], c_pnu[p], F);
-    const R v[9] = {F.a[0].im, F.a[4].im, F.a[8].im, F.a[1].re, F.a[1].im, F.a[2].re, F.a[2].im, F.a[5].re, F.a[5].im};
+    const int mu = c_pmu[p], nu = c_pnu[p];
+    M3<df64> Q;
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q.a[k] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+#pragma unroll 1
+    for (int leaf = 0; leaf < 4; leaf++) {
+        M3<df64> T;
+#pragma unroll 1
+        for (int i = 0; i < 4; i++) {
+            const int f = 4 * leaf + i;
+            int cc[4] = {c[0], c[1], c[2], c[3]};
+            cc[mu] = (cc[mu] + c_ldmu[f] + g.L[mu]) % g.L[mu];
+            cc[nu] = (cc[nu] + c_ldnu[f] + g.L[nu]) % g.L[nu];
+            M3<df64> Lk = link_at<df64>(g, Ue, Uo, cc, c_lnu[f] ? nu : mu);
+            if (c_ldag[f]) {
+                M3<df64> d;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) d.a[a * 3 + b] = cconj(Lk.a[b * 3 + a]);
+                Lk = d;
+            }
+            if (i == 0) {
+                T = Lk;
+            } else {
+                M3<df64> P;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        cx<df64> acc = cmul(T.a[a * 3], Lk.a[b]);
+                        acc = cfma(T.a[a * 3 + 1], Lk.a[3 + b], acc);
+                        acc = cfma(T.a[a * 3 + 2], Lk.a[6 + b], acc);
+                        P.a[a * 3 + b] = acc;
+                    }
+                T = P;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
+    }
+    // F = (Q - Q^+)/8: Im F_aa, then F_01, F_02, F_12
+    const df64 eighth(0.125f, 0.0f);
+    auto fa = [&](int a, int b) { return eighth * (Q.a[a * 3 + b] - cconj(Q.a[b * 3 + a])); };
+    const cx<df64> f01 = fa(0, 1), f02 = fa(0, 2), f12 = fa(1, 2);
+    const df64 v[9] = {fa(0, 0).im, fa(1, 1).im, fa(2, 2).im, f01.re, f01.im, f02.re, f02.im, f12.re, f12.im};
 #pragma unroll
     for (int k = 0; k < 9; k++) Fb[((long long)p * 9 + k) * g.V + lex] = make_float2(v[k].hi, v[k].lo);
 }
@@ -359,7 +314,7 @@ void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void
         // per (site, plane): 12 complex 3x3 products of 198 flops, the leaf sum
         // and (Q - Q^+)/8
         Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 16 * 144 + 6 * 72), (double)e.g.V * 6 * (12 * 198 + 54 + 36));
-        clover_field_kernel<df64><<<blocks_for(6 * e.g.V, 128), 128, 0, e.st>>>(e.g, (const df2 *)Udf[0],
+        clover_field_kernel<<<blocks_for(6 * e.g.V, 128), 128, 0, e.st>>>(e.g, (const df2 *)Udf[0],
                                                                                 (const df2 *)Udf[1],
                                                                                 (float2 *)Fscratch);
     }
