@@ -201,7 +201,7 @@ typedef enum {
     LQ_K_HOP_K2_F64,     /* K2: y_e = D_ee x_e - D_eo t_o (and its fused Richardson form), FP64 */
     LQ_K_HOP_K2_F32,     /* K2, FP32 */
     LQ_K_HOP_OTHER,      /* full-lattice D, prepare, reconstruct, clover apply */
-    LQ_K_CLOVER,         /* clover build, inverse, FP32 copies, export */
+    LQ_K_CLOVER,         /* clover assembly from the field strengths, inverse, rounded copies, export */
     LQ_K_LAYOUT,         /* natural <-> internal layout, precision conversion, gamma5 */
     LQ_K_DOT_F64, LQ_K_DOT_F32,    /* multi-dot products */
     LQ_K_AXPY_F64, LQ_K_AXPY_F32,  /* axpby / multi-axpy */
@@ -210,6 +210,7 @@ typedef enum {
     LQ_K_COPY,           /* device memset / memcpy steps (not kernels) */
     LQ_K_HOP_K1_DF64, LQ_K_HOP_K2_DF64,   /* K1, K2 in df64 */
     LQ_K_DOT_DF64, LQ_K_AXPY_DF64,        /* BLAS-1 in df64 */
+    LQ_K_CLOVER_FIELD,   /* field strengths F_munu of the six planes from the leaves (df64) */
     LQ_K_COUNT
 } lq_kernel_class;
 

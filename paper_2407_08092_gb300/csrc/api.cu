@@ -1328,7 +1328,7 @@ const char *lq_kernel_class_name(int cls)
     static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
                                          "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
                                          "norm", "reduce_finish", "copy", "hop_k1_df64", "hop_k2_df64",
-                                         "dot_df64", "axpy_df64"};
+                                         "dot_df64", "axpy_df64", "clover_field"};
     return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 

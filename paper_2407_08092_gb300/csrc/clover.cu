@@ -311,9 +311,10 @@ static inline unsigned blocks_for(long long n, int threads) { return (unsigned)(
 void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *Fscratch)
 {
     {
-        // per (site, plane): 12 complex 3x3 products of 198 flops, the leaf sum
-        // and (Q - Q^+)/8
-        Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 16 * 144 + 6 * 72), (double)e.g.V * 6 * (12 * 198 + 54 + 36));
+        // unique bytes per site: its four df64 links (4 x 144) and the six F
+        // (6 x 72); per (site, plane): 12 complex 3x3 products of 198 flops,
+        // the leaf sum and (Q - Q^+)/8
+        Launch L_(e, K_CLOVER_FIELD, (double)e.g.V * (4 * 144 + 6 * 72), (double)e.g.V * 6 * (12 * 198 + 54 + 36));
         clover_field_kernel<<<blocks_for(6 * e.g.V, 128), 128, 0, e.st>>>(e.g, (const df2 *)Udf[0],
                                                                                 (const df2 *)Udf[1],
                                                                                 (float2 *)Fscratch);

@@ -18,7 +18,7 @@ enum Prec { P64 = 0, P32 = 1, PDF = 2 };
 enum KClass {
     K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
     K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY,
-    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_COUNT
+    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_COUNT
 };
 
 // Optional CUDA-event timing of every launch (enabled by lq_profile).

@@ -228,7 +228,7 @@ def lq_counters(ctx):
     return n.value, b.value
 
 
-LQ_K_COUNT = 18
+LQ_K_COUNT = 19
 
 
 def lq_profile(ctx, on: bool) -> None:
