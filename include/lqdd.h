@@ -188,6 +188,34 @@ lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, v
 lq_status lq_solve_batch(lq_ctx *ctx, const lq_solver_params *params, int n_rhs, const void *b, void *x,
                          lq_stats *stats);
 
+/* Gradient of the bilinear form b(U) = Re(Y^+ D(U) X) with respect to every
+ * link, for given full spinors X and Y (no paper counterpart: the operator is
+ * the Wilson-clover D of Sec. 2.3, differentiated through its hopping term and
+ * through the plaquette leaves of its clover term).
+ *   G: device complex double [V][4][3][3] in the layout of the gauge field;
+ *   G = coef * (db/dRe U + i db/dIm U), so that db = Re sum conj(G) dU.
+ * Computed in df64 (FP64-accurate).  Needs lq_set_gauge.  Enqueued on the
+ * context's stream; does not synchronise. */
+lq_status lq_force(lq_ctx *ctx, const void *X, const void *Y, double coef, void *G);
+
+/* The pseudofermion action S = phi^+ (D^+ D)^{-1} phi of the gauge field set
+ * by lq_set_gauge (no paper counterpart).  With D^+ = g5 D g5:
+ * Y = D^{-+} phi = g5 D^{-1} g5 phi and X = D^{-1} Y = (D^+ D)^{-1} phi by two
+ * lq_solve calls with `params` (initial guesses zero), and S = ||Y||^2.
+ *   phi: device full spinor; X, Y: device full spinors written by the call (the
+ *   inputs lq_force needs for dS/dU = -2 grad_U Re(Y^+ D X)); S: host double;
+ *   stats: NULL or two entries (the two solves).
+ * Synchronises.  LQ_ERR_NOT_CONVERGED still writes X, Y and S from the last
+ * iterates. */
+lq_status lq_fermion_action(lq_ctx *ctx, const lq_solver_params *params, const void *phi, void *X, void *Y,
+                            double *S, lq_stats *stats);
+
+/* lq_fermion_action followed by lq_force(X, Y, -2): S and its gradient
+ * G = dS/dU ([V][4][3][3] as in lq_force), with X and Y in library-owned
+ * workspace.  Synchronises; LQ_ERR_NOT_CONVERGED as above. */
+lq_status lq_fermion_force(lq_ctx *ctx, const lq_solver_params *params, const void *phi, double *S, void *G,
+                           lq_stats *stats);
+
 /* Copy the clover blocks out for inspection: which = 0 gives C(x), which = 1
  * gives C(x)^{-1} (odd sites only; even entries are zero).  out: device
  * complex double [V][2][6][6], natural site order, block 0 = spins {0,1},
@@ -211,6 +239,7 @@ typedef enum {
     LQ_K_HOP_K1_DF64, LQ_K_HOP_K2_DF64,   /* K1, K2 in df64 */
     LQ_K_DOT_DF64, LQ_K_AXPY_DF64,        /* BLAS-1 in df64 */
     LQ_K_CLOVER_FIELD,   /* field strengths F_munu of the six planes from the leaves (df64) */
+    LQ_K_FORCE,          /* fermion force: clover insertion and per-link gradient (df64) */
     LQ_K_COUNT
 } lq_kernel_class;
 

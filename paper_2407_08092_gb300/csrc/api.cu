@@ -1291,6 +1291,102 @@ lq_status lq_export_clover(lq_ctx *c, int which, void *out)
     });
 }
 
+// G = coef grad_U Re(Y^+ D X) for natural full spinors X, Y (df64 throughout)
+static void force_apply(lq_ctx *c, const void *X, const void *Y, double coef, void *G)
+{
+    Exec e = c->ex();
+    void *xe = field(c, PDF, "force:xe"), *xo = field(c, PDF, "force:xo");
+    void *ye = field(c, PDF, "force:ye"), *yo = field(c, PDF, "force:yo");
+    import_full(e, PDF, X, xe, xo);
+    import_full(e, PDF, Y, ye, yo);
+    const void *Xs[2] = {xe, xo}, *Ys[2] = {ye, yo};
+    const void *U[2] = {c->Udf[0], c->Udf[1]};
+    void *gam = ws(c, "clover:F", (size_t)6 * 9 * 8 * c->g.V);
+    force_insertion(e, Xs, Ys, c->lat.csw, gam);
+    force_links(e, U, Xs, Ys, gam, coef, G);
+    ck_launch(c, "force");
+}
+
+lq_status lq_force(lq_ctx *c, const void *X, const void *Y, double coef, void *G)
+{
+    return guarded(c, [&] {
+        if (!X || !Y || !G) fail(c, LQ_ERR_ARG, "NULL field");
+        need_gauge(c);
+        force_apply(c, X, Y, coef, G);
+    });
+}
+
+// the two solves of the pseudofermion action; X, Y natural full spinors
+static lq_status action_solves(lq_ctx *c, const lq_solver_params *p, const void *phi, void *X, void *Y, double *S,
+                               lq_stats st[2], bool *not_conv)
+{
+    return guarded(c, [&] {
+        if (!p || !phi || !X || !Y || !S) fail(c, LQ_ERR_ARG, "bad argument");
+        need_gauge(c);
+        Exec e = c->ex();
+        const size_t nb = (size_t)c->g.V * 12 * 16;
+        void *w = ws(c, "force:w", nb);
+        auto solve = [&](const void *rhs, void *sol, lq_stats *out) {
+            ck(c, cudaMemsetAsync(sol, 0, nb, c->st), "cudaMemsetAsync");
+            const lq_status r = lq_solve(c, p, rhs, sol, out);
+            if (r == LQ_ERR_NOT_CONVERGED) *not_conv = true;
+            else if (r != LQ_OK) throw Fail{r};
+        };
+        // D^+ = g5 D g5: Y = D^{-+} phi = g5 D^{-1} g5 phi, then X = D^{-1} Y
+        gamma5_nat(e, phi, Y);
+        solve(Y, w, &st[0]);
+        gamma5_nat(e, w, Y);
+        solve(Y, X, &st[1]);
+        nat_norm2(e, Y, c->g.V, c->red, 0);
+        reduce_finish(e, c->red, 0, 1);
+        ck_launch(c, "norm2");
+        *S = fetch(c, 0, 1)[0];
+    });
+}
+
+lq_status lq_fermion_action(lq_ctx *c, const lq_solver_params *p, const void *phi, void *X, void *Y, double *S,
+                            lq_stats *stats)
+{
+    lq_stats st[2] = {};
+    bool not_conv = false;
+    const lq_status s = action_solves(c, p, phi, X, Y, S, st, &not_conv);
+    if (stats) {
+        stats[0] = st[0];
+        stats[1] = st[1];
+    }
+    if (s == LQ_OK && not_conv) {
+        c->err = "tolerance not reached within max_restarts";
+        return LQ_ERR_NOT_CONVERGED;
+    }
+    return s;
+}
+
+lq_status lq_fermion_force(lq_ctx *c, const lq_solver_params *p, const void *phi, double *S, void *G,
+                           lq_stats *stats)
+{
+    lq_stats st[2] = {};
+    bool not_conv = false;
+    lq_status s = guarded(c, [&] {
+        if (!G) fail(c, LQ_ERR_ARG, "NULL gradient");
+        need_gauge(c);
+        const size_t nb = (size_t)c->g.V * 12 * 16;
+        void *y = ws(c, "force:y", nb), *x = ws(c, "force:x", nb);
+        const lq_status r = action_solves(c, p, phi, x, y, S, st, &not_conv);
+        if (r != LQ_OK) throw Fail{r};
+        force_apply(c, x, y, -2.0, G);
+        sync(c);
+    });
+    if (stats) {
+        stats[0] = st[0];
+        stats[1] = st[1];
+    }
+    if (s == LQ_OK && not_conv) {
+        c->err = "tolerance not reached within max_restarts";
+        return LQ_ERR_NOT_CONVERGED;
+    }
+    return s;
+}
+
 lq_status lq_profile(lq_ctx *c, int on)
 {
     if (!c) return LQ_ERR_ARG;
@@ -1328,7 +1424,7 @@ const char *lq_kernel_class_name(int cls)
     static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
                                          "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
                                          "norm", "reduce_finish", "copy", "hop_k1_df64", "hop_k2_df64",
-                                         "dot_df64", "axpy_df64", "clover_field"};
+                                         "dot_df64", "axpy_df64", "clover_field", "force"};
     return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 

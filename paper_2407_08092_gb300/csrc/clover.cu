@@ -17,26 +17,10 @@
 // copies by rounding.  The build is split in two launches: one thread per
 // (site, plane) computes the four leaves and F of that plane into a scratch
 // array, then one thread per site assembles the two 6x6 blocks.
+#include "leaves.cuh"
 #include "lq_kernels.h"
 
 namespace lq {
-
-template <typename R>
-struct M3 {
-    cx<R> a[9];
-};
-
-// the link U_mu at coordinates c, read from the internal per-parity copies
-template <typename R>
-__device__ __forceinline__ M3<R> link_at(const Geom &g, const typename St<R>::vec *Ue,
-                                         const typename St<R>::vec *Uo, const int c[4], int mu)
-{
-    const long long lex = c[0] + (long long)g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
-    const int parity = (c[0] + c[1] + c[2] + c[3]) & 1;
-    M3<R> m;
-    load_link(parity ? Uo : Ue, g.stride, mu, lex >> 1, m.a);
-    return m;
-}
 
 __device__ __forceinline__ void store_pair(double2 *p, double a, double b) { *p = make_double2(a, b); }
 __device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.hi, a.lo, b.hi, b.lo}; }
@@ -45,24 +29,8 @@ __device__ __forceinline__ bool positive(df64 d) { return df_positive(d); }
 
 // Field strength of one plane at one site per thread: F = (Q - Q^+)/8 is
 // anti-Hermitian, so 9 reals describe it: Im F_aa (a = 0,1,2), then F_01, F_02,
-// F_12 (re, im).  Stored as df64 pairs in F[plane][9][V].
-__constant__ int c_pmu[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int c_pnu[6] = {1, 2, 2, 3, 3, 3};
-
-// The 16 link factors of the four leaves of plane (mu, nu), leaf by leaf:
-//   leaf 1: U_mu(x)       U_nu(x+mu)        U_mu(x+nu)^+     U_nu(x)^+
-//   leaf 2: U_nu(x)       U_mu(x-mu+nu)^+   U_nu(x-mu)^+     U_mu(x-mu)
-//   leaf 3: U_mu(x-mu)^+  U_nu(x-mu-nu)^+   U_mu(x-mu-nu)    U_nu(x-nu)
-//   leaf 4: U_nu(x-nu)^+  U_mu(x-nu)        U_nu(x+mu-nu)    U_mu(x)^+
-// as the site offset along mu and nu, whether the link points along nu, and
-// whether it enters as U^+.  Walking this table lets one inlined 3x3 product
-// serve all twelve products (the df64 code stays small enough for the
-// instruction cache).
-__constant__ signed char c_ldmu[16] = {0, 1, 0, 0, 0, -1, -1, -1, -1, -1, -1, 0, 0, 0, 1, 0};
-__constant__ signed char c_ldnu[16] = {0, 0, 1, 0, 0, 1, 0, 0, 0, -1, -1, -1, -1, -1, -1, 0};
-__constant__ unsigned char c_lnu[16] = {0, 1, 0, 1, 1, 0, 1, 0, 0, 1, 0, 1, 1, 0, 1, 0};
-__constant__ unsigned char c_ldag[16] = {0, 0, 1, 1, 0, 1, 1, 0, 1, 1, 0, 0, 1, 0, 0, 1};
-
+// F_12 (re, im).  Stored as df64 pairs in F[plane][9][V].  The leaf factors
+// come from the tables of leaves.cuh.
 __global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const df2 *__restrict__ Ue,
                                                            const df2 *__restrict__ Uo, float2 *Fb)
 {

@@ -18,7 +18,7 @@ enum Prec { P64 = 0, P32 = 1, PDF = 2 };
 enum KClass {
     K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
     K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY,
-    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_COUNT
+    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_FORCE, K_COUNT
 };
 
 // Optional CUDA-event timing of every launch (enabled by lq_profile).
@@ -103,6 +103,15 @@ void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag);
 void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32);
 // natural export: out[V][2][6][6] c128 from FP64 packed blocks (null parity pointer -> zeros)
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
+
+// ---- fermion force (force.cu) ----------------------------------------------
+// X, Y: internal df64 full fields (even, odd).  Gam: device scratch of
+// 6 * 9 * V * 8 bytes.  G: natural c128 [V][4][3][3], G = coef grad_U Re(Y^+ D X).
+void force_insertion(const Exec &e, const void *X[2], const void *Y[2], double csw, void *Gam);
+void force_links(const Exec &e, const void *Udf[2], const void *X[2], const void *Y[2], const void *Gam,
+                 double coef, void *G);
+// out = g5 in on natural full spinors (in == out allowed)
+void gamma5_nat(const Exec &e, const void *in, void *out);
 
 // ---- hopping term (dslash.cu) ----------------------------------------------
 // Modes of the fused hopping kernel; acc = sum of the eight hops into x (the

@@ -210,6 +210,47 @@ def lq_solve_batch(ctx, params: lq_solver_params, n_rhs: int, b, x):
     return s, list(st)
 
 
+_lib.lq_force.argtypes = [_P, _P, _P, ctypes.c_double, _P]
+_lib.lq_force.restype = ctypes.c_int
+_lib.lq_fermion_force.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, ctypes.POINTER(ctypes.c_double), _P,
+                                  ctypes.POINTER(lq_stats)]
+_lib.lq_fermion_force.restype = ctypes.c_int
+
+
+def lq_force(ctx, X, Y, G, coef: float = 1.0):
+    """G = coef * grad_U Re(Y^+ D X) for full spinors X, Y ([V, 4, 3] complex128
+    CUDA tensors); G is a [V, 4, 3, 3] complex128 CUDA tensor."""
+    _check(ctx, _lib.lq_force(ctx, _ptr(X), _ptr(Y), float(coef), _ptr(G)))
+
+
+_lib.lq_fermion_action.argtypes = [_P, ctypes.POINTER(lq_solver_params), _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(lq_stats)]
+_lib.lq_fermion_action.restype = ctypes.c_int
+
+
+def lq_fermion_action(ctx, params: lq_solver_params, phi, X, Y):
+    """S = phi^+ (D^+ D)^{-1} phi; writes X = (D^+ D)^{-1} phi and Y = D X.
+    Returns (status, S, [stats of the two solves]); raises on every status but
+    OK and NOT_CONVERGED."""
+    S = ctypes.c_double()
+    st = (lq_stats * 2)()
+    s = _lib.lq_fermion_action(ctx, ctypes.byref(params), _ptr(phi), _ptr(X), _ptr(Y), ctypes.byref(S), st)
+    if s not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctx, s)
+    return s, S.value, list(st)
+
+
+def lq_fermion_force(ctx, params: lq_solver_params, phi, G):
+    """S = phi^+ (D^+ D)^{-1} phi and G = dS/dU.  Returns (status, S, [stats of
+    the two solves]); raises on every status but OK and NOT_CONVERGED."""
+    S = ctypes.c_double()
+    st = (lq_stats * 2)()
+    s = _lib.lq_fermion_force(ctx, ctypes.byref(params), _ptr(phi), ctypes.byref(S), _ptr(G), st)
+    if s not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctx, s)
+    return s, S.value, list(st)
+
+
 def make_batch_params(tol=1e-10, restart=16, max_restarts=10, smooth_n=8, smooth_tol=1e-5) -> lq_solver_params:
     """Parameters of lq_solve_batch: df64 defect correction around batched FP32 GMRES(restart)."""
     return make_params(solver=LQ_SOLVER_GMRES, prec=LQ_DF64, tol=tol, restart=restart, max_restarts=max_restarts,
@@ -228,7 +269,7 @@ def lq_counters(ctx):
     return n.value, b.value
 
 
-LQ_K_COUNT = 19
+LQ_K_COUNT = 20
 
 
 def lq_profile(ctx, on: bool) -> None:

@@ -21,7 +21,7 @@ def main():
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32, 2 df64")
     ap.add_argument("--apps", type=int, default=3)
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch"])
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force"])
     ap.add_argument("--nrhs", type=int, default=12)
     a = ap.parse_args()
     L = tuple(int(v) for v in a.lattice.split(","))
@@ -48,6 +48,18 @@ def main():
         out = max(s.rel_resid_true for s in st)
         print("outer corrections", [s.iters for s in st], "inner steps", [s.inner_iters for s in st],
               "ms", round(st[0].time_ms, 2))
+    elif a.mode == "force":
+        X = torch.from_numpy(synth.gaussian_spinor(V, 71)).cuda()
+        Y = torch.from_numpy(synth.gaussian_spinor(V, 72)).cuda()
+        G = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(a.apps):
+            lqdd.lq_force(ctx, X, Y, G, coef=-2.0)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("force kernel pair", round(ev[0].elapsed_time(ev[1]) / a.apps, 3), "ms per call")
+        out = float(G.abs().max())
     else:
         b = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()
         x = torch.zeros_like(b)

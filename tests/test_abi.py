@@ -56,6 +56,16 @@ def test_binding_names_match_header(lib_path):
         assert hasattr(lqdd.library(), n)
 
 
+def test_kernel_class_names(lib_path):
+    from paper_2407_08092_gb300 import lqdd
+    names = [lqdd.lq_kernel_class_name(c) for c in range(lqdd.LQ_K_COUNT)]
+    assert all(names) and len(set(names)) == len(names)
+    assert lqdd.lq_kernel_class_name(lqdd.LQ_K_COUNT) == ""
+    header = open(os.path.join(ROOT, "include", "lqdd.h")).read()
+    enum = header[header.index("LQ_K_HOP_K1_F64 = 0"):header.index("LQ_K_COUNT")]
+    assert len(re.findall(r"LQ_K_[A-Z0-9_]+", enum)) == lqdd.LQ_K_COUNT
+
+
 def test_struct_layouts_match_header(tmp_path):
     from paper_2407_08092_gb300 import lqdd
     probe = tmp_path / "probe.c"
