@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct lq_ctx lq_ctx;
+typedef struct lq_group lq_group;
 
 typedef enum {
     LQ_OK = 0,
@@ -184,9 +185,49 @@ lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, v
  *   initial guesses on entry.  stats: NULL or n_rhs entries (cycles = iters = outer
  *   corrections of that right-hand side, inner_iters = inner Arnoldi steps launched
  *   for it; time, bytes and launches are those of the whole call).  Synchronises.
- *   LQ_ERR_NOT_CONVERGED still writes every x_r and fills stats. */
+ *   LQ_ERR_NOT_CONVERGED still writes every x_r and fills stats.
+ * This is lq_solve_group on a one-member group that the context keeps. */
 lq_status lq_solve_batch(lq_ctx *ctx, const lq_solver_params *params, int n_rhs, const void *b, void *x,
                          lq_stats *stats);
+
+/* A group of contexts (lattices of any sizes, on one device) whose right-hand
+ * sides are solved together by lq_solve_group.  The group does not own its
+ * members: destroy the group before any of them.  `stream`: the cudaStream_t
+ * of the group's calls (NULL: the legacy default stream).  Errors of group
+ * calls are described by lq_last_error of the first member. */
+lq_status lq_group_create(lq_group **out, lq_ctx *const *members, int n_members, void *stream);
+lq_status lq_group_destroy(lq_group *grp);
+
+/* Solve D_l x_{l,r} = b_{l,r} for every member l and each of its n_rhs[l]
+ * right-hand sides (1..256 each, at most 1024 in total), with the method of
+ * lq_solve_batch applied to all of them at once (Sec. 3.3 names multiple
+ * right-hand sides as the cache-friendly extension; here they also span
+ * lattices of different sizes): odd-even reduction (Eq. 2) per right-hand side;
+ * df64 defect correction per member; corrections from one batched FP32
+ * GMRES(m) (Algorithm 2 per system, Givens least squares on the device) whose
+ * every operator launch is a single persistent grid walking a work table of
+ * (lattice, site block, right-hand sides) tiles over all members, and whose
+ * cycles replay captured CUDA graphs.  The first solve of a new layout (members'
+ * n_rhs, restart) lays out the workspace and, unless disabled, autotunes the
+ * tile shape, grid and BLAS blocking on the group's own buffers.
+ *   params: as lq_solve_batch (prec LQ_DF64, inner_prec LQ_F32, restart 1..64).
+ *   b[l], x[l]: device [n_rhs[l]][V_l][4][3] complex double; x holds initial
+ *   guesses.  stats: NULL or sum(n_rhs) entries, member by member.
+ * Synchronises.  LQ_ERR_NOT_CONVERGED still writes every x and fills stats. */
+lq_status lq_solve_group(lq_group *grp, const lq_solver_params *params, const int *n_rhs, const void *const *b,
+                         void *const *x, lq_stats *stats);
+
+/* Autotuning of the group's launch shapes on (default) or off (fixed shapes:
+ * 32 sites x 4 right-hand sides per tile, twice the resident blocks); drops the
+ * current layout and captured graphs. */
+lq_status lq_group_set_autotune(lq_group *grp, int on);
+
+/* The launch shapes in use after a solve: sites per tile of the batched hop
+ * (right-hand sides per tile = 128 / sites), its grid, BLAS blocks per system,
+ * and the measured times of the chosen hop pair and BLAS pair (0 if untuned).
+ * LQ_ERR_STATE before the first solve.  Any pointer may be NULL. */
+lq_status lq_group_tuning(lq_group *grp, int *sites_per_tile, int *grid, int *blas_blocks, double *hop_ms,
+                          double *blas_ms);
 
 /* Gradient of the bilinear form b(U) = Re(Y^+ D(U) X) with respect to every
  * link, for given full spinors X and Y (no paper counterpart: the operator is

@@ -60,22 +60,7 @@ struct lq_ctx {
     std::vector<void *> owned;
     std::string err;
     Prof prof;
-    // batched (multi right-hand side) solver state: FP32 workspace, device
-    // Givens state and the captured CUDA graph of one inner GMRES cycle
-    struct Batch {
-        int N = 0, m = 0;
-        void *V = nullptr, *T = nullptr, *X = nullptr, *B = nullptr;
-        BatchRed br{};
-        KState ks{};
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-        // captured segments of a cycle: [0] start, [1..nseg] Arnoldi steps, [nseg+1] finish
-        std::vector<cudaGraphExec_t> gexec;
-        std::vector<long long> cap_launches;
-        std::vector<double> cap_bytes;
-        double *h = nullptr;   // pinned host mirror: est[N] then target[N]
-        int *hact = nullptr;   // pinned host mirror of the active flags
-    } batch;
+    lq_group *self_group = nullptr;   // the one-member group behind lq_solve_batch
     Exec ex() { return Exec{g, st, &ctr, &prof}; }
 };
 
@@ -589,10 +574,10 @@ void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
     if (p->smoother == LQ_SMOOTH_GMRES && !(p->smooth_tol >= 0.0)) fail(c, LQ_ERR_ARG, "smooth_tol < 0");
 }
 
-// ---- batched right-hand sides ------------------------------------------------------
+// ---- batched right-hand sides over one or several lattices -------------------------
 
-// out = D_S in for N consecutive fields: one batched K1 and one batched K2
-// launch, each site's links and clover read once for all right-hand sides
+// out = D_S in for N consecutive fields of one lattice: one batched K1 and one
+// batched K2 launch (the df64 defect of the batched solve)
 void op_schur_n(lq_ctx *c, int prec, const void *in, void *out, void *t, int N)
 {
     Exec e = c->ex();
@@ -611,188 +596,450 @@ void op_schur_n(lq_ctx *c, int prec, const void *in, void *out, void *t, int N)
     hop(e, k2);
 }
 
-// FP32 workspace, reduction scratch and device Givens state for N right-hand
-// sides and cycle length m; the captured graph is dropped when they change
-void batch_setup(lq_ctx *c, int N, int m)
+}  // namespace
+
+// A batched solve over the right-hand sides of one or several lattices (contexts
+// on one device).  The inner FP32 GMRES treats every right-hand side of every
+// member as one system of a batch: each operator launch is one persistent grid
+// walking a work table over all members' sites and right-hand sides, the BLAS
+// launches cover all systems, and the Givens bookkeeping runs on the device, so
+// that a cycle is a short sequence of captured CUDA graphs.  The outer df64
+// defect correction runs per member.
+struct lq_group {
+    std::vector<lq_ctx *> mem;
+    cudaStream_t user = nullptr;   // stream of the group's calls
+    cudaStream_t st = nullptr;     // private stream (graph capture)
+    cudaEvent_t ev = nullptr;
+    bool autotune = true;
+    // layout of the current signature: right-hand sides per member, cycle length
+    std::vector<int> nrhs;
+    int N = 0, m = 0;
+    long long mf = 0;              // float4 vectors per multi-field
+    std::vector<long long> off;    // first field of each member in a multi-field
+    std::vector<int> first;        // first system of each member
+    Segs S;
+    LatDesc *desc = nullptr;
+    int4 *tiles = nullptr;
+    int ntiles = 0, max_tiles = 0, blas_default = 1, blas_max = 1;
+    double k1_bytes = 0, k2_bytes = 0, k1_flops = 0, k2_flops = 0;
+    struct {
+        int spt = 32, grid = 0, blas = 0;
+        float hop_ms = 0.0f, blas_ms = 0.0f;
+        bool tuned = false;
+    } tune;
+    void *V = nullptr, *T = nullptr, *X = nullptr, *B = nullptr;
+    BatchRed br{};
+    KState ks{};
+    std::vector<BatchRed> mbr;     // per-member df64 norms of the outer iteration
+    std::vector<cudaGraphExec_t> gexec;
+    std::vector<long long> cap_launches;
+    std::vector<double> cap_bytes;
+    double *h = nullptr;           // pinned: est / norms [N], targets [N], norms [N]
+    int *hact = nullptr;           // pinned: active flags [N]
+    std::vector<void *> owned;
+};
+
+namespace {
+
+// the context that records the group's errors, launches and profile: member 0
+lq_ctx *gctx(lq_group *G) { return G->mem[0]; }
+
+Exec gexec(lq_group *G)
 {
-    auto &B = c->batch;
-    if (!B.st) {
-        ck(c, cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking), "cudaStreamCreate");
-        ck(c, cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming), "cudaEventCreate");
-        ck(c, cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming), "cudaEventCreate");
-    }
-    if (B.N == N && B.m == m) return;
-    for (cudaGraphExec_t g : B.gexec)
-        if (g) cudaGraphExecDestroy(g);
-    B.gexec.clear();
-    B.cap_launches.clear();
-    B.cap_bytes.clear();
-    if (B.h) cudaFreeHost(B.h);
-    if (B.hact) cudaFreeHost(B.hact);
-    B.h = nullptr;
-    B.hact = nullptr;
-    ck(c, cudaMallocHost((void **)&B.h, sizeof(double) * 2 * N), "cudaMallocHost");
-    ck(c, cudaMallocHost((void **)&B.hact, sizeof(int) * N), "cudaMallocHost");
-    const size_t f32 = spinor_bytes(c->g, P32);
-    B.V = ws(c, "b:V", (size_t)(m + 1) * N * f32);
-    B.T = ws(c, "b:T", (size_t)N * f32);
-    B.X = ws(c, "b:X", (size_t)N * f32);
-    B.B = ws(c, "b:B", (size_t)N * f32);
-    B.br.blocks = batch_blocks(c->g, N);
-    B.br.pitch = 2 * (2 * m + 2);
-    B.br.partial = (double *)ws(c, "b:part", sizeof(double) * (size_t)N * B.br.blocks * B.br.pitch);
-    B.br.out = (double *)ws(c, "b:out", sizeof(double) * (size_t)N * B.br.pitch);
-    KState &k = B.ks;
-    k.N = N;
-    k.m = m;
-    k.H = (double2 *)ws(c, "b:H", sizeof(double2) * (size_t)N * (m + 1) * m);
-    k.cs = (double *)ws(c, "b:cs", sizeof(double) * (size_t)N * m);
-    k.sn = (double2 *)ws(c, "b:sn", sizeof(double2) * (size_t)N * m);
-    k.g = (double2 *)ws(c, "b:g", sizeof(double2) * (size_t)N * (m + 1));
-    k.y = (double2 *)ws(c, "b:y", sizeof(double2) * (size_t)N * m);
-    k.active = (int *)ws(c, "b:act", sizeof(int) * N);
-    k.kused = (int *)ws(c, "b:ku", sizeof(int) * N);
-    k.nanflag = (int *)ws(c, "b:nan", sizeof(int));
-    k.scale = (double *)ws(c, "b:sc", sizeof(double) * N);
-    k.est = (double *)ws(c, "b:est", sizeof(double) * N);
-    k.target = (double *)ws(c, "b:tg", sizeof(double) * N);
-    B.N = N;
-    B.m = m;
+    lq_ctx *c = G->mem[0];
+    return Exec{c->g, G->st, &c->ctr, &c->prof};
 }
 
-// One cycle of batched GMRES(m) in FP32 on D_S (Algorithm 2 for each right-hand
-// side), in three kinds of segment, each a fixed launch sequence without host
+void *galloc(lq_group *G, size_t bytes)
+{
+    lq_ctx *c = gctx(G);
+    void *p = nullptr;
+    ck(c, cudaMalloc(&p, bytes), "cudaMalloc");
+    G->owned.push_back(p);
+    ck(c, cudaMemsetAsync(p, 0, bytes, G->st), "cudaMemsetAsync");
+    return p;
+}
+
+// drop everything that depends on the layout
+void group_release(lq_group *G)
+{
+    if (G->st) cudaStreamSynchronize(G->st);
+    for (cudaGraphExec_t g : G->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    G->gexec.clear();
+    G->cap_launches.clear();
+    G->cap_bytes.clear();
+    for (void *p : G->owned) cudaFree(p);
+    G->owned.clear();
+    if (G->h) cudaFreeHost(G->h);
+    if (G->hact) cudaFreeHost(G->hact);
+    G->h = nullptr;
+    G->hact = nullptr;
+    G->nrhs.clear();
+    G->N = G->m = 0;
+    G->tune.tuned = false;
+}
+
+// the work table of the batched hop for `spt` sites per tile: per member, per
+// site block, its right-hand-side groups (so the tiles of one site block follow
+// one another)
+void group_tiles(lq_group *G, int spt)
+{
+    const int rpt = kHopBlock / spt;
+    std::vector<int4> t;
+    for (size_t l = 0; l < G->mem.size(); l++) {
+        const long long sb = (G->mem[l]->g.Vh + spt - 1) / spt;
+        const int groups = (G->nrhs[l] + rpt - 1) / rpt;
+        for (long long b = 0; b < sb; b++)
+            for (int q = 0; q < groups; q++) t.push_back(make_int4((int)l, (int)b, q * rpt, 0));
+    }
+    lq_ctx *c = gctx(G);
+    if ((int)t.size() > G->max_tiles) fail(c, LQ_ERR_STATE, "work table larger than its buffer");
+    ck(c, cudaMemcpyAsync(G->tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, G->st),
+       "cudaMemcpyAsync H2D");
+    ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
+    G->ntiles = (int)t.size();
+    G->tune.spt = spt;
+}
+
+// persistent grid: `factor` times the resident blocks of the whole GPU (0: one
+// block per tile)
+int group_grid(lq_group *G, int factor)
+{
+    if (factor == 0) return G->ntiles;
+    int sms = 0;
+    ck(gctx(G), cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gctx(G)->device), "cudaDeviceGetAttribute");
+    const long long g = (long long)factor * hop_group_resident() * sms;
+    return (int)(g < G->ntiles ? g : G->ntiles);
+}
+
+void group_setup(lq_group *G, const std::vector<int> &nrhs, int m)
+{
+    lq_ctx *c = gctx(G);
+    if (!G->st) {
+        ck(c, cudaStreamCreateWithFlags(&G->st, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(c, cudaEventCreateWithFlags(&G->ev, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (G->nrhs == nrhs && G->m == m) return;
+    group_release(G);
+    const int M = (int)G->mem.size();
+    int N = 0;
+    long long mf = 0, maxfs = 0;
+    double sites = 0.0;
+    G->off.assign(M, 0);
+    G->first.assign(M, 0);
+    std::vector<longlong2> seg;
+    std::vector<LatDesc> desc(M);
+    G->k1_bytes = G->k2_bytes = G->k1_flops = G->k2_flops = 0.0;
+    long long max_tiles = 0;
+    for (int l = 0; l < M; l++) {
+        lq_ctx *ml = G->mem[l];
+        const long long fs = 6 * ml->g.stride;
+        G->off[l] = mf;
+        G->first[l] = N;
+        for (int r = 0; r < nrhs[l]; r++) seg.push_back(make_longlong2(mf + r * fs, fs));
+        LatDesc &d = desc[l];
+        d.g = ml->g;
+        d.U[0] = (const float4 *)ml->U32[0];
+        d.U[1] = (const float4 *)ml->U32[1];
+        d.clov[0] = (const float4 *)ml->C32[0];
+        d.clov[1] = (const float4 *)ml->Ci32;
+        d.off = mf;
+        d.fs = fs;
+        d.nrhs = nrhs[l];
+        mf += nrhs[l] * fs;
+        N += nrhs[l];
+        maxfs = fs > maxfs ? fs : maxfs;
+        sites += (double)nrhs[l] * ml->g.Vh;
+        G->k1_bytes += hop_bytes(HOP_K1, P32, nrhs[l], (double)ml->g.Vh);
+        G->k2_bytes += hop_bytes(HOP_K2, P32, nrhs[l], (double)ml->g.Vh);
+        G->k1_flops += hop_flops(HOP_K1, (double)ml->g.Vh * nrhs[l]);
+        G->k2_flops += hop_flops(HOP_K2, (double)ml->g.Vh * nrhs[l]);
+        max_tiles += (ml->g.Vh + 15) / 16 * ((nrhs[l] + 7) / 8) + (ml->g.Vh + 127) / 128 * nrhs[l] +
+                     (ml->g.Vh + 63) / 64 * ((nrhs[l] + 1) / 2) + (ml->g.Vh + 31) / 32 * ((nrhs[l] + 3) / 4);
+    }
+    G->N = N;
+    G->m = m;
+    G->mf = mf;
+    G->max_tiles = (int)max_tiles;
+    G->blas_default = batch_blocks(maxfs, N);
+    G->blas_max = 2 * G->blas_default;
+    G->S.seg = (const longlong2 *)galloc(G, sizeof(longlong2) * N);
+    ck(c, cudaMemcpyAsync((void *)G->S.seg, seg.data(), sizeof(longlong2) * N, cudaMemcpyHostToDevice, G->st),
+       "cudaMemcpyAsync H2D");
+    G->desc = (LatDesc *)galloc(G, sizeof(LatDesc) * M);
+    ck(c, cudaMemcpyAsync(G->desc, desc.data(), sizeof(LatDesc) * M, cudaMemcpyHostToDevice, G->st),
+       "cudaMemcpyAsync H2D");
+    ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
+    G->S.n = 0;
+    G->S.sites = sites;
+    G->S.blocks = G->blas_default;
+    G->tiles = (int4 *)galloc(G, sizeof(int4) * (size_t)max_tiles);
+    const size_t mfb = (size_t)mf * 16;
+    G->V = galloc(G, (size_t)(m + 1) * mfb);
+    G->T = galloc(G, mfb);
+    G->X = galloc(G, mfb);
+    G->B = galloc(G, mfb);
+    G->br.blocks = G->blas_default;
+    G->br.pitch = 2 * (2 * m + 2);
+    G->br.partial = (double *)galloc(G, sizeof(double) * (size_t)N * G->blas_max * G->br.pitch);
+    G->br.out = (double *)galloc(G, sizeof(double) * (size_t)N * G->br.pitch);
+    KState &k = G->ks;
+    k.N = N;
+    k.m = m;
+    k.H = (double2 *)galloc(G, sizeof(double2) * (size_t)N * (m + 1) * m);
+    k.cs = (double *)galloc(G, sizeof(double) * (size_t)N * m);
+    k.sn = (double2 *)galloc(G, sizeof(double2) * (size_t)N * m);
+    k.g = (double2 *)galloc(G, sizeof(double2) * (size_t)N * (m + 1));
+    k.y = (double2 *)galloc(G, sizeof(double2) * (size_t)N * m);
+    k.active = (int *)galloc(G, sizeof(int) * N);
+    k.kused = (int *)galloc(G, sizeof(int) * N);
+    k.nanflag = (int *)galloc(G, sizeof(int));
+    k.scale = (double *)galloc(G, sizeof(double) * N);
+    k.est = (double *)galloc(G, sizeof(double) * N);
+    k.target = (double *)galloc(G, sizeof(double) * N);
+    G->mbr.assign(M, BatchRed{});
+    for (int l = 0; l < M; l++) {
+        BatchRed &b = G->mbr[l];
+        b.blocks = batch_blocks(12 * G->mem[l]->g.stride, nrhs[l]);
+        b.pitch = 2;
+        b.partial = (double *)galloc(G, sizeof(double) * (size_t)nrhs[l] * b.blocks * b.pitch);
+        b.out = (double *)galloc(G, sizeof(double) * (size_t)nrhs[l] * b.pitch);
+    }
+    ck(c, cudaMallocHost((void **)&G->h, sizeof(double) * 3 * N), "cudaMallocHost");
+    ck(c, cudaMallocHost((void **)&G->hact, sizeof(int) * N), "cudaMallocHost");
+    G->nrhs = nrhs;
+    group_tiles(G, 32);
+    G->tune.grid = group_grid(G, 2);
+    G->tune.blas = G->blas_default;
+    G->tune.tuned = false;
+}
+
+// out = D_S in for every system (two persistent launches over the work table)
+void group_schur(lq_group *G, const void *in, void *out)
+{
+    Exec e = gexec(G);
+    hop_group(e, HOP_K1, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, in, nullptr, G->T, G->k1_bytes,
+              G->k1_flops);
+    hop_group(e, HOP_K2, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, G->T, in, out, G->k2_bytes,
+              G->k2_flops);
+}
+
+void group_set_blas(lq_group *G, int blocks)
+{
+    G->tune.blas = blocks;
+    G->S.blocks = blocks;
+    G->br.blocks = blocks;
+}
+
+// The autotuner: times every candidate launch shape on the group's own buffers
+// (CUDA events, after a warm-up launch) and keeps the fastest.
+//   batched hop: sites per tile 16, 32, 64, 128 (with 8, 4, 2, 1 right-hand
+//     sides per tile) x grid = 1 or 2 times the resident blocks (persistent) or
+//     one block per tile;
+//   batched BLAS: blocks per system 1/2, 1, 2 times the default, on a
+//     multi-dot and a multi-axpy over min(m, 8) basis vectors.
+// Launch counts and bytes of the trials are not recorded.
+void group_tune(lq_group *G)
+{
+    lq_ctx *c = gctx(G);
+    const Counters saved = c->ctr;
+    const bool prof = c->prof.on;
+    c->prof.on = false;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ck(c, cudaEventCreate(&a), "cudaEventCreate");
+    ck(c, cudaEventCreate(&b), "cudaEventCreate");
+    auto timed = [&](auto fn) {
+        fn();
+        cudaEventRecord(a, G->st);
+        for (int i = 0; i < 3; i++) fn();
+        cudaEventRecord(b, G->st);
+        ck(c, cudaEventSynchronize(b), "cudaEventSynchronize");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms / 3.0f;
+    };
+    float best = 1e30f;
+    int best_spt = 32, best_factor = 2;
+    for (int spt : {32, 64, 16, 128}) {
+        group_tiles(G, spt);
+        for (int factor : {1, 2, 0}) {
+            G->tune.grid = group_grid(G, factor);
+            const float t = timed([&] { group_schur(G, G->X, G->V); });
+            if (t < best) {
+                best = t;
+                best_spt = spt;
+                best_factor = factor;
+            }
+        }
+    }
+    group_tiles(G, best_spt);
+    G->tune.grid = group_grid(G, best_factor);
+    G->tune.hop_ms = best;
+    const int nv = G->m < 8 ? G->m : 8;
+    Exec e = gexec(G);
+    float bbest = 1e30f;
+    int bblocks = G->blas_default;
+    for (int blocks : {G->blas_default, G->blas_default / 2, 2 * G->blas_default}) {
+        if (blocks < 1 || blocks > G->blas_max) continue;
+        group_set_blas(G, blocks);
+        const float t = timed([&] {
+            bdot(e, G->S, G->V, G->mf, nv, G->T, G->N, G->br, 0);
+            baxpy(e, G->S, G->V, G->mf, nv, G->br.out, G->br.pitch / 2, -1, G->T, G->N, &G->br, nv);
+        });
+        if (t < bbest) {
+            bbest = t;
+            bblocks = blocks;
+        }
+    }
+    group_set_blas(G, bblocks);
+    G->tune.blas_ms = bbest;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ck(c, cudaMemsetAsync(G->T, 0, (size_t)G->mf * 16, G->st), "cudaMemsetAsync");
+    ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
+    c->ctr = saved;
+    c->prof.on = prof;
+    G->tune.tuned = true;
+}
+
+// One cycle of batched GMRES(m) in FP32 on D_S (Algorithm 2 for each system), in
+// three kinds of segment, each a fixed launch sequence without host
 // synchronisation:
 //   start:  r = B - D_S X, beta = ||r||, g = beta e_1, V_0 = r / beta
-//   steps:  Arnoldi steps [k0, k1): w = D_S v_k, CGS2, Givens on the device, v_{k+1}
+//   steps:  Arnoldi steps [k0, k1): w = D_S v_k, one Gram-Schmidt pass with the
+//           new norm fused, Givens on the device, v_{k+1}
 //   finish: y = R^{-1} g, X += V y
 static constexpr int BATCH_SEG = 4;   // Arnoldi steps per segment
 
-void batch_start(lq_ctx *c)
+void group_start(lq_group *G)
 {
-    auto &B = c->batch;
-    const int N = B.N;
-    Exec e = c->ex();
-    op_schur_n(c, P32, B.X, B.V, B.T, N);
-    axpby(e, P32, 1.0, 0.0, B.B, -1.0, 0.0, B.V, N);   // V_0 = B - D_S X
-    bnorm(e, P32, B.V, N, B.br, 0);
-    bfinish(e, B.br, N, 0, 1);
-    ks_init(e, B.ks, B.br.out, B.br.pitch);
-    bscale(e, B.V, B.ks.scale, B.V, N);
+    Exec e = gexec(G);
+    group_schur(G, G->X, G->V);
+    bxmy(e, G->S, G->B, G->V, G->N);   // V_0 = B - D_S X
+    bnorm(e, P32, G->S, G->V, G->N, G->br, 0);
+    bfinish(e, G->br, G->N, 0, 1);
+    ks_init(e, G->ks, G->br.out, G->br.pitch);
+    bscale(e, G->S, G->V, G->ks.scale, G->V, G->N);
 }
 
-void batch_steps(lq_ctx *c, int k0, int k1)
+void group_steps(lq_group *G, int k0, int k1)
 {
-    auto &B = c->batch;
-    const int N = B.N;
-    Exec e = c->ex();
-    const long long vjs = (long long)N * 6 * c->g.stride;   // float4 vectors between basis vectors
-    const size_t f32 = spinor_bytes(c->g, P32);
-    auto Vj = [&](int j) { return (char *)B.V + (size_t)j * N * f32; };
+    Exec e = gexec(G);
+    auto Vj = [&](int j) { return (char *)G->V + (size_t)j * G->mf * 16; };
     for (int k = k0; k < k1; k++) {
-        op_schur_n(c, P32, Vj(k), Vj(k + 1), B.T, N);
-        // one classical Gram-Schmidt pass with the new norm fused (FP32 inner solver)
+        group_schur(G, Vj(k), Vj(k + 1));
         const int nv = k + 1;
-        bdot(e, B.V, vjs, nv, Vj(k + 1), N, B.br, 0);
-        bfinish(e, B.br, N, 0, nv);
-        baxpy(e, B.V, vjs, nv, B.br.out, B.br.pitch / 2, -1, Vj(k + 1), N, &B.br, nv);
-        bfinish(e, B.br, N, nv, 1);
-        ks_step(e, B.ks, k, 1, B.br.out, B.br.pitch);
-        bscale(e, Vj(k + 1), B.ks.scale, Vj(k + 1), N);
+        bdot(e, G->S, G->V, G->mf, nv, Vj(k + 1), G->N, G->br, 0);
+        bfinish(e, G->br, G->N, 0, nv);
+        baxpy(e, G->S, G->V, G->mf, nv, G->br.out, G->br.pitch / 2, -1, Vj(k + 1), G->N, &G->br, nv);
+        bfinish(e, G->br, G->N, nv, 1);
+        ks_step(e, G->ks, k, 1, G->br.out, G->br.pitch);
+        bscale(e, G->S, Vj(k + 1), G->ks.scale, Vj(k + 1), G->N);
     }
 }
 
-void batch_finish(lq_ctx *c)
+void group_finish(lq_group *G)
 {
-    auto &B = c->batch;
-    Exec e = c->ex();
-    const long long vjs = (long long)B.N * 6 * c->g.stride;
-    ks_solve(e, B.ks);
-    baxpy(e, B.V, vjs, B.m, (const double *)B.ks.y, B.m, +1, B.X, B.N, nullptr, 0);
+    Exec e = gexec(G);
+    ks_solve(e, G->ks);
+    baxpy(e, G->S, G->V, G->mf, G->m, (const double *)G->ks.y, G->m, +1, G->X, G->N, nullptr, 0);
 }
 
 // Segment `id` (0 start, 1..nseg steps, nseg+1 finish): replayed from its CUDA
 // graph, captured on first use; launched eagerly while per-launch profiling is
 // on.  Launches and bytes are counted on every replay.
-void batch_segment(lq_ctx *c, int id)
+void group_segment(lq_group *G, int id)
 {
-    auto &B = c->batch;
-    const int nseg = (B.m + BATCH_SEG - 1) / BATCH_SEG;
+    lq_ctx *c = gctx(G);
+    const int nseg = (G->m + BATCH_SEG - 1) / BATCH_SEG;
     auto body = [&]() {
-        if (id == 0) batch_start(c);
-        else if (id <= nseg) batch_steps(c, (id - 1) * BATCH_SEG, std::min(B.m, id * BATCH_SEG));
-        else batch_finish(c);
+        if (id == 0) group_start(G);
+        else if (id <= nseg) group_steps(G, (id - 1) * BATCH_SEG, std::min(G->m, id * BATCH_SEG));
+        else group_finish(G);
     };
     if (c->prof.on) {
         body();
         ck_launch(c, "batched segment");
         return;
     }
-    if ((int)B.gexec.size() < nseg + 2) {
-        B.gexec.resize(nseg + 2, nullptr);
-        B.cap_launches.resize(nseg + 2, 0);
-        B.cap_bytes.resize(nseg + 2, 0.0);
+    if ((int)G->gexec.size() < nseg + 2) {
+        G->gexec.resize(nseg + 2, nullptr);
+        G->cap_launches.resize(nseg + 2, 0);
+        G->cap_bytes.resize(nseg + 2, 0.0);
     }
-    if (!B.gexec[id]) {
+    if (!G->gexec[id]) {
         const long long l0 = c->ctr.launches;
         const double b0 = c->ctr.bytes;
-        ck(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        ck(c, cudaStreamBeginCapture(G->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         body();
         cudaGraph_t graph = nullptr;
-        const cudaError_t err = cudaStreamEndCapture(c->st, &graph);
+        const cudaError_t err = cudaStreamEndCapture(G->st, &graph);
         ck(c, err, "cudaStreamEndCapture");
-        const cudaError_t ierr = cudaGraphInstantiate(&B.gexec[id], graph, 0);
+        const cudaError_t ierr = cudaGraphInstantiate(&G->gexec[id], graph, 0);
         cudaGraphDestroy(graph);
         ck(c, ierr, "cudaGraphInstantiate");
-        B.cap_launches[id] = c->ctr.launches - l0;
-        B.cap_bytes[id] = c->ctr.bytes - b0;
+        G->cap_launches[id] = c->ctr.launches - l0;
+        G->cap_bytes[id] = c->ctr.bytes - b0;
         c->ctr.launches = l0;
         c->ctr.bytes = b0;
     }
-    ck(c, cudaGraphLaunch(B.gexec[id], c->st), "cudaGraphLaunch");
-    c->ctr.launches += B.cap_launches[id];
-    c->ctr.bytes += B.cap_bytes[id];
+    ck(c, cudaGraphLaunch(G->gexec[id], G->st), "cudaGraphLaunch");
+    c->ctr.launches += G->cap_launches[id];
+    c->ctr.bytes += G->cap_bytes[id];
 }
 
-// One inner cycle: start, step segments until every right-hand side has left
-// the cycle (host check of the active flags between segments), finish.
-// Returns the Arnoldi steps launched.
-int batch_run_cycle(lq_ctx *c)
+// One inner cycle: start, step segments until every system has left the cycle
+// (host check of the active flags between segments), finish.  Returns the
+// Arnoldi steps launched.
+int group_run_cycle(lq_group *G)
 {
-    auto &B = c->batch;
-    const int nseg = (B.m + BATCH_SEG - 1) / BATCH_SEG;
-    batch_segment(c, 0);
+    lq_ctx *c = gctx(G);
+    const int nseg = (G->m + BATCH_SEG - 1) / BATCH_SEG;
+    group_segment(G, 0);
     int steps = 0;
     for (int j = 1; j <= nseg; j++) {
-        ck(c, cudaMemcpyAsync(B.hact, B.ks.active, sizeof(int) * B.N, cudaMemcpyDeviceToHost, c->st),
+        ck(c, cudaMemcpyAsync(G->hact, G->ks.active, sizeof(int) * G->N, cudaMemcpyDeviceToHost, G->st),
            "cudaMemcpyAsync D2H");
-        sync(c);
+        ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
         bool any = false;
-        for (int r = 0; r < B.N; r++) any = any || B.hact[r];
+        for (int r = 0; r < G->N; r++) any = any || G->hact[r];
         if (!any) break;
-        batch_segment(c, j);
-        steps += std::min(B.m, j * BATCH_SEG) - (j - 1) * BATCH_SEG;
+        group_segment(G, j);
+        steps += std::min(G->m, j * BATCH_SEG) - (j - 1) * BATCH_SEG;
     }
-    batch_segment(c, nseg + 1);
+    group_segment(G, nseg + 1);
     return steps;
 }
 
-// Runs the batched solve on the context's private stream (capturable), ordered
-// after the caller's stream on entry and before it on exit.
-struct OnBatchStream {
-    lq_ctx *c;
-    cudaStream_t user;
-    explicit OnBatchStream(lq_ctx *c_) : c(c_), user(c_->st)
+// Runs a group solve on the group's private stream (capturable), with every
+// member's work redirected there; ordered after the group's stream and every
+// member's stream on entry, and before them on exit.
+struct OnGroupStream {
+    lq_group *G;
+    std::vector<cudaStream_t> saved;
+    explicit OnGroupStream(lq_group *G_) : G(G_)
     {
-        ck(c, cudaEventRecord(c->batch.ev_in, user), "cudaEventRecord");
-        ck(c, cudaStreamWaitEvent(c->batch.st, c->batch.ev_in, 0), "cudaStreamWaitEvent");
-        c->st = c->batch.st;
+        lq_ctx *c = gctx(G);
+        ck(c, cudaEventRecord(G->ev, G->user), "cudaEventRecord");
+        ck(c, cudaStreamWaitEvent(G->st, G->ev, 0), "cudaStreamWaitEvent");
+        for (lq_ctx *m : G->mem) {
+            ck(c, cudaEventRecord(G->ev, m->st), "cudaEventRecord");
+            ck(c, cudaStreamWaitEvent(G->st, G->ev, 0), "cudaStreamWaitEvent");
+        }
+        for (lq_ctx *m : G->mem) {
+            saved.push_back(m->st);
+            m->st = G->st;
+        }
     }
-    ~OnBatchStream()
+    ~OnGroupStream()
     {
-        cudaEventRecord(c->batch.ev_out, c->st);
-        c->st = user;
-        cudaStreamWaitEvent(user, c->batch.ev_out, 0);
+        cudaEventRecord(G->ev, G->st);
+        for (size_t i = 0; i < G->mem.size(); i++) {
+            G->mem[i]->st = saved[i];
+            cudaStreamWaitEvent(saved[i], G->ev, 0);
+        }
+        cudaStreamWaitEvent(G->user, G->ev, 0);
     }
 };
 
@@ -880,18 +1127,12 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
 lq_status lq_destroy(lq_ctx *c)
 {
     if (!c) return LQ_ERR_ARG;
+    if (c->self_group) lq_group_destroy(c->self_group);
     cudaStreamSynchronize(c->st);
     for (void *p : c->owned)
         if (p) cudaFree(p);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     for (cudaEvent_t ev : c->prof.pool) cudaEventDestroy(ev);
-    for (cudaGraphExec_t g : c->batch.gexec)
-        if (g) cudaGraphExecDestroy(g);
-    if (c->batch.hact) cudaFreeHost(c->batch.hact);
-    if (c->batch.ev_in) cudaEventDestroy(c->batch.ev_in);
-    if (c->batch.ev_out) cudaEventDestroy(c->batch.ev_out);
-    if (c->batch.st) cudaStreamDestroy(c->batch.st);
-    if (c->batch.h) cudaFreeHost(c->batch.h);
     delete c;
     return LQ_OK;
 }
@@ -1147,15 +1388,91 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
     return s;
 }
 
-lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const void *b, void *x, lq_stats *stats)
+// ---- batched solves over one or several lattices ------------------------------------
+
+lq_status lq_group_create(lq_group **out, lq_ctx *const *members, int n_members, void *stream)
 {
+    if (!out || !members || n_members < 1 || n_members > 64) return LQ_ERR_ARG;
+    for (int i = 0; i < n_members; i++) {
+        if (!members[i]) return LQ_ERR_ARG;
+        if (members[i]->device != members[0]->device) {
+            members[0]->err = "group members must share one device";
+            return LQ_ERR_ARG;
+        }
+        for (int j = 0; j < i; j++)
+            if (members[j] == members[i]) {
+                members[0]->err = "a context appears twice in the group";
+                return LQ_ERR_ARG;
+            }
+    }
+    lq_group *G = new (std::nothrow) lq_group;
+    if (!G) return LQ_ERR_OOM;
+    G->mem.assign(members, members + n_members);
+    G->user = (cudaStream_t)stream;
+    *out = G;
+    return LQ_OK;
+}
+
+lq_status lq_group_destroy(lq_group *G)
+{
+    if (!G) return LQ_ERR_ARG;
+    group_release(G);
+    if (G->ev) cudaEventDestroy(G->ev);
+    if (G->st) cudaStreamDestroy(G->st);
+    delete G;
+    return LQ_OK;
+}
+
+lq_status lq_group_set_autotune(lq_group *G, int on)
+{
+    if (!G) return LQ_ERR_ARG;
+    return guarded(gctx(G), [&] {
+        G->autotune = on != 0;
+        group_release(G);   // the next solve lays out, tunes (or not) and captures afresh
+    });
+}
+
+lq_status lq_group_tuning(lq_group *G, int *sites_per_tile, int *grid, int *blas_blocks, double *hop_ms,
+                          double *blas_ms)
+{
+    if (!G) return LQ_ERR_ARG;
+    if (!G->N) {
+        gctx(G)->err = "no solve has run on this group yet";
+        return LQ_ERR_STATE;
+    }
+    if (sites_per_tile) *sites_per_tile = G->tune.spt;
+    if (grid) *grid = G->tune.grid;
+    if (blas_blocks) *blas_blocks = G->tune.blas;
+    if (hop_ms) *hop_ms = G->tune.tuned ? G->tune.hop_ms : 0.0;
+    if (blas_ms) *blas_ms = G->tune.tuned ? G->tune.blas_ms : 0.0;
+    return LQ_OK;
+}
+
+lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rhs, const void *const *b,
+                         void *const *x, lq_stats *stats)
+{
+    if (!G) return LQ_ERR_ARG;
+    lq_ctx *c = gctx(G);
+    const int M = (int)G->mem.size();
     const auto t0 = std::chrono::steady_clock::now();
-    const long long l0 = c ? c->ctr.launches : 0;
-    const double by0 = c ? c->ctr.bytes : 0.0;
-    std::vector<lq_stats> st(n_rhs > 0 ? n_rhs : 0);
+    std::vector<long long> l0(M);
+    std::vector<double> by0(M);
+    for (int l = 0; l < M; l++) {
+        l0[l] = G->mem[l]->ctr.launches;
+        by0[l] = G->mem[l]->ctr.bytes;
+    }
+    int Ntot = 0;
+    if (n_rhs)
+        for (int l = 0; l < M; l++) Ntot += n_rhs[l] > 0 ? n_rhs[l] : 0;
+    std::vector<lq_stats> st(Ntot);
     bool not_conv = false;
     lq_status s = guarded(c, [&] {
-        if (!b || !x || !p || n_rhs < 1 || n_rhs > 256) fail(c, LQ_ERR_ARG, "bad argument");
+        if (!b || !x || !p || !n_rhs) fail(c, LQ_ERR_ARG, "bad argument");
+        for (int l = 0; l < M; l++) {
+            if (n_rhs[l] < 1 || n_rhs[l] > 256 || !b[l] || !x[l]) fail(c, LQ_ERR_ARG, "bad right-hand sides");
+            need_gauge(G->mem[l]);
+        }
+        if (Ntot > 1024) fail(c, LQ_ERR_ARG, "more than 1024 systems");
         if (p->restart < 1 || p->restart > 64) fail(c, LQ_ERR_ARG, "restart (inner cycle length) out of range 1..64");
         if (p->max_restarts < 1) fail(c, LQ_ERR_ARG, "max_restarts < 1");
         if (!(p->tol > 0.0) || !std::isfinite(p->tol)) fail(c, LQ_ERR_ARG, "tol must be positive");
@@ -1163,114 +1480,161 @@ lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const 
         if (p->inner_prec != LQ_F32) fail(c, LQ_ERR_ARG, "the batched inner solver runs in LQ_F32");
         if (p->smooth_n < 1) fail(c, LQ_ERR_ARG, "smooth_n (inner cycles) < 1");
         if (!(p->smooth_tol > 0.0 && p->smooth_tol < 1.0)) fail(c, LQ_ERR_ARG, "smooth_tol must be in (0, 1)");
-        need_gauge(c);
-        const int N = n_rhs;
-        batch_setup(c, N, p->restart);
-        auto &B = c->batch;
-        OnBatchStream on(c);
-        Exec e = c->ex();
-        const size_t fw = spinor_bytes(c->g, PDF), f32 = spinor_bytes(c->g, P32);
-        const size_t nat = (size_t)c->g.V * 12 * sizeof(double2);
-        char *BE = (char *)ws(c, "bw:be", N * fw), *BO = (char *)ws(c, "bw:bo", N * fw);
-        char *BH = (char *)ws(c, "bw:bh", N * fw), *XE = (char *)ws(c, "bw:xe", N * fw);
-        char *XO = (char *)ws(c, "bw:xo", N * fw), *R = (char *)ws(c, "bw:r", N * fw);
-        char *T = (char *)ws(c, "bw:t", N * fw), *E = (char *)ws(c, "bw:e", N * fw);
-        // prepare (Eq. 2) every right-hand side
-        for (int r = 0; r < N; r++) {
-            import_full(e, PDF, (const char *)b + r * nat, BE + r * fw, BO + r * fw);
-            import_full(e, PDF, (const char *)x + r * nat, XE + r * fw, XO + r * fw);
-            op_prepare(c, PDF, BE + r * fw, BO + r * fw, BH + r * fw, T);
+        group_setup(G, std::vector<int>(n_rhs, n_rhs + M), p->restart);
+        OnGroupStream on(G);
+        if (G->autotune && !G->tune.tuned) group_tune(G);
+        const int N = G->N;
+        // per member: df64 workspaces of its right-hand sides
+        struct MW {
+            char *BE, *BO, *BH, *XE, *XO, *R, *T, *E;
+            size_t fw, nat;
+        };
+        std::vector<MW> w(M);
+        for (int l = 0; l < M; l++) {
+            lq_ctx *ml = G->mem[l];
+            const int n = n_rhs[l];
+            MW &q = w[l];
+            q.fw = spinor_bytes(ml->g, PDF);
+            q.nat = (size_t)ml->g.V * 12 * sizeof(double2);
+            q.BE = (char *)ws(ml, "bw:be", n * q.fw);
+            q.BO = (char *)ws(ml, "bw:bo", n * q.fw);
+            q.BH = (char *)ws(ml, "bw:bh", n * q.fw);
+            q.XE = (char *)ws(ml, "bw:xe", n * q.fw);
+            q.XO = (char *)ws(ml, "bw:xo", n * q.fw);
+            q.R = (char *)ws(ml, "bw:r", n * q.fw);
+            q.T = (char *)ws(ml, "bw:t", n * q.fw);
+            q.E = (char *)ws(ml, "bw:e", n * q.fw);
+            Exec e = ml->ex();
+            // prepare (Eq. 2) every right-hand side
+            for (int r = 0; r < n; r++) {
+                import_full(e, PDF, (const char *)b[l] + r * q.nat, q.BE + r * q.fw, q.BO + r * q.fw);
+                import_full(e, PDF, (const char *)x[l] + r * q.nat, q.XE + r * q.fw, q.XO + r * q.fw);
+                op_prepare(ml, PDF, q.BE + r * q.fw, q.BO + r * q.fw, q.BH + r * q.fw, q.T);
+            }
         }
-        auto norms = [&](const void *F, std::vector<double> &out) {
-            bnorm(e, PDF, F, N, B.br, 0);
-            bfinish(e, B.br, N, 0, 1);
-            ck(c, cudaMemcpy2DAsync(B.h, sizeof(double), B.br.out, sizeof(double) * B.br.pitch, sizeof(double), N,
-                                    cudaMemcpyDeviceToHost, c->st),
-               "cudaMemcpy2DAsync");
-            sync(c);
+        // df64 norms of one field per right-hand side, all members, into out[N]
+        auto norms = [&](char *MW::*f, std::vector<double> &out) {
+            for (int l = 0; l < M; l++) {
+                lq_ctx *ml = G->mem[l];
+                Exec e = ml->ex();
+                Segs S1;
+                S1.n = 12 * ml->g.stride;
+                S1.sites = (double)n_rhs[l] * ml->g.Vh;
+                bnorm(e, PDF, S1, w[l].*f, n_rhs[l], G->mbr[l], 0);
+                bfinish(e, G->mbr[l], n_rhs[l], 0, 1);
+                ck(c, cudaMemcpy2DAsync(G->h + 2 * N + G->first[l], sizeof(double), G->mbr[l].out,
+                                        sizeof(double) * G->mbr[l].pitch, sizeof(double), n_rhs[l],
+                                        cudaMemcpyDeviceToHost, G->st),
+                   "cudaMemcpy2DAsync");
+            }
+            ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
             out.resize(N);
-            for (int r = 0; r < N; r++) out[r] = std::sqrt(B.h[r]);
+            for (int k = 0; k < N; k++) out[k] = std::sqrt(G->h[2 * N + k]);
         };
         std::vector<double> bn, rn;
-        norms(BH, bn);
+        norms(&MW::BH, bn);
         std::vector<int> outer(N, 0);
         std::vector<long long> inner(N, 0);
         bool all = false;
         for (int it = 0; it <= p->max_restarts; it++) {
-            // defect: R = b_hat - D_S x in df64
-            op_schur_n(c, PDF, XE, R, T, N);
-            axpby(e, PDF, 1.0, 0.0, BH, -1.0, 0.0, R, N);
-            norms(R, rn);
+            // defect: R = b_hat - D_S x in df64, per member
+            for (int l = 0; l < M; l++) {
+                lq_ctx *ml = G->mem[l];
+                op_schur_n(ml, PDF, w[l].XE, w[l].R, w[l].T, n_rhs[l]);
+                axpby(ml->ex(), PDF, 1.0, 0.0, w[l].BH, -1.0, 0.0, w[l].R, n_rhs[l]);
+            }
+            norms(&MW::R, rn);
             all = true;
-            for (int r = 0; r < N; r++) {
-                if (!std::isfinite(rn[r])) fail(c, LQ_ERR_NAN, "NaN/Inf in a residual");
-                st[r].rel_resid = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
-                if (st[r].rel_resid > p->tol) all = false;
+            for (int k = 0; k < N; k++) {
+                if (!std::isfinite(rn[k])) fail(c, LQ_ERR_NAN, "NaN/Inf in a residual");
+                st[k].rel_resid = bn[k] > 0 ? rn[k] / bn[k] : 0.0;
+                if (st[k].rel_resid > p->tol) all = false;
             }
             if (all || it == p->max_restarts) break;
             // correction: D_S e = R to smooth_tol (relative) with batched FP32 GMRES
-            for (int r = 0; r < N; r++) convert(e, PDF, R + r * fw, P32, (char *)B.B + r * f32);
-            ck(c, cudaMemsetAsync(B.X, 0, N * f32, c->st), "cudaMemsetAsync");
-            for (int r = 0; r < N; r++) {
-                const bool done = st[r].rel_resid <= p->tol;
-                B.h[N + r] = done ? rn[r] * 2.0 : p->smooth_tol * rn[r];   // converged ones stay idle
-                if (!done) outer[r]++;
+            for (int l = 0; l < M; l++) {
+                Exec e = G->mem[l]->ex();
+                const long long fs = 6 * G->mem[l]->g.stride;
+                for (int r = 0; r < n_rhs[l]; r++)
+                    convert(e, PDF, w[l].R + r * w[l].fw, P32, (float4 *)G->B + G->off[l] + r * fs);
             }
-            ck(c, cudaMemcpyAsync(B.ks.target, B.h + N, sizeof(double) * N, cudaMemcpyHostToDevice, c->st),
+            ck(c, cudaMemsetAsync(G->X, 0, (size_t)G->mf * 16, G->st), "cudaMemsetAsync");
+            for (int k = 0; k < N; k++) {
+                const bool done = st[k].rel_resid <= p->tol;
+                G->h[N + k] = done ? rn[k] * 2.0 : p->smooth_tol * rn[k];   // converged ones stay idle
+                if (!done) outer[k]++;
+            }
+            ck(c, cudaMemcpyAsync(G->ks.target, G->h + N, sizeof(double) * N, cudaMemcpyHostToDevice, G->st),
                "cudaMemcpyAsync H2D");
-            ck(c, cudaMemsetAsync(B.ks.nanflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
+            ck(c, cudaMemsetAsync(G->ks.nanflag, 0, sizeof(int), G->st), "cudaMemsetAsync");
             for (int cyc = 0; cyc < p->smooth_n; cyc++) {
-                const int steps = batch_run_cycle(c);
-                ck(c, cudaMemcpyAsync(B.h, B.ks.est, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st),
+                const int steps = group_run_cycle(G);
+                ck(c, cudaMemcpyAsync(G->h, G->ks.est, sizeof(double) * N, cudaMemcpyDeviceToHost, G->st),
                    "cudaMemcpyAsync D2H");
-                sync(c);
+                ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
                 bool inner_done = true;
-                for (int r = 0; r < N; r++) {
-                    if (st[r].rel_resid > p->tol) inner[r] += steps;
-                    if (B.h[r] > B.h[N + r]) inner_done = false;
+                for (int k = 0; k < N; k++) {
+                    if (st[k].rel_resid > p->tol) inner[k] += steps;
+                    if (G->h[k] > G->h[N + k]) inner_done = false;
                 }
                 if (inner_done) break;
             }
-            int nanflag = 0;
-            ck(c, cudaMemcpyAsync(&B.hact[0], B.ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+            ck(c, cudaMemcpyAsync(&G->hact[0], G->ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost, G->st),
                "cudaMemcpyAsync D2H");
-            sync(c);
-            nanflag = B.hact[0];
-            if (nanflag) fail(c, LQ_ERR_NAN, "NaN/Inf in the batched inner solve");
-            for (int r = 0; r < N; r++) convert(e, P32, (char *)B.X + r * f32, PDF, E + r * fw);
-            axpby(e, PDF, 1.0, 0.0, E, 1.0, 0.0, XE, N);
+            ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
+            if (G->hact[0]) fail(c, LQ_ERR_NAN, "NaN/Inf in the batched inner solve");
+            for (int l = 0; l < M; l++) {
+                lq_ctx *ml = G->mem[l];
+                Exec e = ml->ex();
+                const long long fs = 6 * ml->g.stride;
+                for (int r = 0; r < n_rhs[l]; r++)
+                    convert(e, P32, (const float4 *)G->X + G->off[l] + r * fs, PDF, w[l].E + r * w[l].fw);
+                axpby(e, PDF, 1.0, 0.0, w[l].E, 1.0, 0.0, w[l].XE, n_rhs[l]);
+            }
         }
         not_conv = !all;
         // reconstruct (Eq. 2), export, true residual of every right-hand side
-        void *ye = field(c, PDF, "bw:ye"), *yo = field(c, PDF, "bw:yo");
-        for (int r = 0; r < N; r++) {
-            op_reconstruct(c, PDF, BO + r * fw, XE + r * fw, XO + r * fw);
-            export_full(e, PDF, XE + r * fw, XO + r * fw, (char *)x + r * nat);
-            op_full(c, PDF, XE + r * fw, XO + r * fw, ye, yo);
-            axpby(e, PDF, 1.0, 0.0, BE + r * fw, -1.0, 0.0, ye);
-            axpby(e, PDF, 1.0, 0.0, BO + r * fw, -1.0, 0.0, yo);
-            norm2(e, PDF, ye, c->red, 0);
-            norm2(e, PDF, yo, c->red, 1);
-            norm2(e, PDF, BE + r * fw, c->red, 2);
-            norm2(e, PDF, BO + r * fw, c->red, 3);
-            reduce_finish(e, c->red, 0, 4);
-            const double *hv = fetch(c, 0, 4);
-            const double bb = hv[4] + hv[6];
-            st[r].rel_resid_true = bb > 0 ? std::sqrt((hv[0] + hv[2]) / bb) : 0.0;
-            if (!std::isfinite(st[r].rel_resid_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in a true residual");
-            st[r].cycles = outer[r];
-            st[r].iters = outer[r];
-            st[r].inner_iters = inner[r];
+        for (int l = 0; l < M; l++) {
+            lq_ctx *ml = G->mem[l];
+            Exec e = ml->ex();
+            const MW &q = w[l];
+            void *ye = field(ml, PDF, "bw:ye"), *yo = field(ml, PDF, "bw:yo");
+            for (int r = 0; r < n_rhs[l]; r++) {
+                const int k = G->first[l] + r;
+                op_reconstruct(ml, PDF, q.BO + r * q.fw, q.XE + r * q.fw, q.XO + r * q.fw);
+                export_full(e, PDF, q.XE + r * q.fw, q.XO + r * q.fw, (char *)x[l] + r * q.nat);
+                op_full(ml, PDF, q.XE + r * q.fw, q.XO + r * q.fw, ye, yo);
+                axpby(e, PDF, 1.0, 0.0, q.BE + r * q.fw, -1.0, 0.0, ye);
+                axpby(e, PDF, 1.0, 0.0, q.BO + r * q.fw, -1.0, 0.0, yo);
+                norm2(e, PDF, ye, ml->red, 0);
+                norm2(e, PDF, yo, ml->red, 1);
+                norm2(e, PDF, q.BE + r * q.fw, ml->red, 2);
+                norm2(e, PDF, q.BO + r * q.fw, ml->red, 3);
+                reduce_finish(e, ml->red, 0, 4);
+                const double *hv = fetch(ml, 0, 4);
+                const double bb = hv[4] + hv[6];
+                st[k].rel_resid_true = bb > 0 ? std::sqrt((hv[0] + hv[2]) / bb) : 0.0;
+                if (!std::isfinite(st[k].rel_resid_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in a true residual");
+                st[k].cycles = outer[k];
+                st[k].iters = outer[k];
+                st[k].inner_iters = inner[k];
+            }
         }
-        sync(c);
+        ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
     });
-    if (c && stats) {
+    if (stats) {
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        for (int r = 0; r < n_rhs; r++) {
-            st[r].time_ms = ms;
-            st[r].launches = c->ctr.launches - l0;
-            st[r].bytes = c->ctr.bytes - by0;
-            stats[r] = st[r];
+        long long nl = 0;
+        double nb = 0.0;
+        for (int l = 0; l < M; l++) {
+            nl += G->mem[l]->ctr.launches - l0[l];
+            nb += G->mem[l]->ctr.bytes - by0[l];
+        }
+        for (int k = 0; k < Ntot; k++) {
+            st[k].time_ms = ms;
+            st[k].launches = nl;
+            st[k].bytes = nb;
+            stats[k] = st[k];
         }
     }
     if (s == LQ_OK && not_conv) {
@@ -1278,6 +1642,20 @@ lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const 
         return LQ_ERR_NOT_CONVERGED;
     }
     return s;
+}
+
+lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const void *b, void *x, lq_stats *stats)
+{
+    if (!c) return LQ_ERR_ARG;
+    if (!c->self_group) {
+        lq_ctx *one[1] = {c};
+        const lq_status s = lq_group_create(&c->self_group, one, 1, c->st);
+        if (s != LQ_OK) return s;
+    }
+    c->self_group->user = c->st;
+    void *xs[1] = {x};
+    const void *bs[1] = {b};
+    return lq_solve_group(c->self_group, p, &n_rhs, bs, xs, stats);
 }
 
 lq_status lq_export_clover(lq_ctx *c, int which, void *out)

@@ -1,19 +1,21 @@
-// Batched (multi right-hand side) BLAS-1 and the device-side Arnoldi/Givens
-// bookkeeping of the batched GMRES cycle.
+// Batched (multi right-hand side, multi lattice) BLAS-1 and the device-side
+// Arnoldi/Givens bookkeeping of the batched GMRES cycle.
 //
-// A batch holds N right-hand sides.  Field r of a batch of fields starts
-// r * n vectors after the first (n = vectors per field).  The Krylov basis of
-// the batched GMRES is stored vector-major: basis vector j of right-hand side
-// r is field j * N + r, so that the N fields of one basis vector are
-// contiguous and one batched operator launch maps V_j to V_{j+1}.
+// A batch holds N systems (right-hand sides, possibly of lattices of
+// different sizes).  System r's field occupies vectors [off_r, off_r + len_r)
+// of a "multi-field" (Segs; the uniform layout off_r = r * n, len_r = n when
+// no table is given).  The Krylov basis of the batched GMRES is stored
+// vector-major: basis vector j is one multi-field, the next one vjs vectors
+// further, so that one batched operator launch maps V_j to V_{j+1} for every
+// system.
 //
-// Every kernel here runs a grid (blocks, N): blockIdx.y selects the
-// right-hand side.  Reductions keep the deterministic two-stage scheme of the
-// single-right-hand-side kernels, per right-hand side.
+// Every kernel here runs a grid (blocks, N): blockIdx.y selects the system and
+// the blocks stride over its field.  Reductions keep the deterministic
+// two-stage scheme of the single-right-hand-side kernels, per system.
 //
 // The Givens bookkeeping (Algorithm 2's least-squares problem) runs on the
-// device, one thread per right-hand side, so that a whole GMRES cycle is a
-// fixed sequence of launches with no host synchronisation.
+// device, one thread per system, so that a whole GMRES cycle is a fixed
+// sequence of launches with no host synchronisation.
 #include <cmath>
 
 #include "lq_kernels.h"
@@ -21,6 +23,19 @@
 namespace lq {
 
 static constexpr int BT = 256;
+
+// offset and length (vectors) of system r
+__device__ __forceinline__ void seg_of(const longlong2 *seg, long long n, int r, long long &off, long long &len)
+{
+    if (seg) {
+        const longlong2 t = seg[r];
+        off = t.x;
+        len = t.y;
+    } else {
+        off = (long long)r * n;
+        len = n;
+    }
+}
 
 __device__ __forceinline__ float2 cdot4(float4 v, float4 w, float2 a)
 {
@@ -54,17 +69,20 @@ __device__ __forceinline__ void bsum(float v[N], float *sh)
 
 // partial[(r * gridDim.x + block) * pitch + 2 * (slot0 + j) + re/im] = block share of (v_jr, w_r)
 template <int NJ>
-__global__ void __launch_bounds__(BT, 4) bdot_kernel(const float4 *__restrict__ V, long long vjs, long long n,
+__global__ void __launch_bounds__(BT, 4) bdot_kernel(const float4 *__restrict__ V, long long vjs,
+                                                     const longlong2 *seg, long long n,
                                                      const float4 *__restrict__ w, double *partial, int pitch,
                                                      int slot0)
 {
     __shared__ float sh[(BT / 32) * 2 * NJ];
     const int r = blockIdx.y;
-    const float4 *Vr = V + r * n, *wr = w + r * n;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
+    const float4 *Vr = V + off, *wr = w + off;
     float acc[2 * NJ];
 #pragma unroll
     for (int i = 0; i < 2 * NJ; i++) acc[i] = 0.0f;
-    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
         const float4 wv = __ldg(wr + i);
 #pragma unroll
         for (int j = 0; j < NJ; j++) {
@@ -85,8 +103,9 @@ __global__ void __launch_bounds__(BT, 4) bdot_kernel(const float4 *__restrict__ 
 // y_r += sign * sum_j c_{r,j} v_{j,r}; with NORM also the partials of ||y_r||^2.
 // Coefficients (complex doubles) for right-hand side r start at c + r * cstride.
 template <bool NORM>
-__global__ void __launch_bounds__(BT, 4) baxpy_kernel(const float4 *__restrict__ V, long long vjs, long long n,
-                                                      int nv, const double2 *__restrict__ c, int cstride, float sign,
+__global__ void __launch_bounds__(BT, 4) baxpy_kernel(const float4 *__restrict__ V, long long vjs,
+                                                      const longlong2 *seg, long long n, int nv,
+                                                      const double2 *__restrict__ c, int cstride, float sign,
                                                       float4 *y, double *partial, int pitch, int slot)
 {
     __shared__ float csr[256], csi[256];
@@ -98,10 +117,12 @@ __global__ void __launch_bounds__(BT, 4) baxpy_kernel(const float4 *__restrict__
         csi[j] = sign * (float)cj.y;
     }
     __syncthreads();
-    const float4 *Vr = V + r * n;
-    float4 *yr = y + r * n;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
+    const float4 *Vr = V + off;
+    float4 *yr = y + off;
     float nrm[1] = {0.0f};
-    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
         float4 yv = yr[i];
         for (int j = 0; j < nv; j++) {
             const float4 v = __ldg(Vr + j * vjs + i);
@@ -124,14 +145,16 @@ __global__ void __launch_bounds__(BT, 4) baxpy_kernel(const float4 *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(BT) bnorm_kernel(const float4 *__restrict__ w, long long n, double *partial,
-                                                   int pitch, int slot)
+__global__ void __launch_bounds__(BT) bnorm_kernel(const float4 *__restrict__ w, const longlong2 *seg, long long n,
+                                                   double *partial, int pitch, int slot)
 {
     __shared__ float sh[BT / 32];
     const int r = blockIdx.y;
-    const float4 *wr = w + r * n;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
+    const float4 *wr = w + off;
     float nrm[1] = {0.0f};
-    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
         const float4 v = __ldg(wr + i);
         nrm[0] = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, nrm[0]))));
     }
@@ -148,14 +171,16 @@ __device__ __forceinline__ df64 bshfl_df(df64 v, int o)
 {
     return df64(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
 }
-__global__ void __launch_bounds__(BT) bnorm_df_kernel(const df2 *__restrict__ w, long long n, double *partial,
-                                                      int pitch, int slot)
+__global__ void __launch_bounds__(BT) bnorm_df_kernel(const df2 *__restrict__ w, const longlong2 *seg, long long n,
+                                                      double *partial, int pitch, int slot)
 {
     __shared__ df64 sh[BT / 32];
     const int r = blockIdx.y;
-    const df2 *wr = w + r * n;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
+    const df2 *wr = w + off;
     df64 acc = df64(0.0f, 0.0f);
-    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
         const cx<df64> v = df2_cx(ldg(wr + i));
         acc = fma(v.re, v.re, fma(v.im, v.im, acc));
     }
@@ -192,19 +217,40 @@ __global__ void __launch_bounds__(BT) bfinish_kernel(const double *__restrict__ 
     }
 }
 
-// y_r = s_r x_r (FP32 fields, device scale per right-hand side)
-__global__ void __launch_bounds__(BT) bscale_kernel(const float4 *x, long long n, const double *s, float4 *y)
+// y_r = s_r x_r (FP32 fields, device scale per system)
+__global__ void __launch_bounds__(BT) bscale_kernel(const float4 *x, const longlong2 *seg, long long n,
+                                                    const double *s, float4 *y)
 {
     const int r = blockIdx.y;
-    const long long i = blockIdx.x * (long long)BT + threadIdx.x;
-    if (i >= n) return;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
     const float f = (float)s[r];
-    float4 v = x[r * n + i];
-    v.x *= f;
-    v.y *= f;
-    v.z *= f;
-    v.w *= f;
-    y[r * n + i] = v;
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
+        float4 v = x[off + i];
+        v.x *= f;
+        v.y *= f;
+        v.z *= f;
+        v.w *= f;
+        y[off + i] = v;
+    }
+}
+
+// y_r = x_r - y_r (FP32 fields)
+__global__ void __launch_bounds__(BT) bxmy_kernel(const float4 *__restrict__ x, const longlong2 *seg, long long n,
+                                                  float4 *y)
+{
+    const int r = blockIdx.y;
+    long long off, len;
+    seg_of(seg, n, r, off, len);
+    for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
+        const float4 a = __ldg(x + off + i);
+        float4 b = y[off + i];
+        b.x = a.x - b.x;
+        b.y = a.y - b.y;
+        b.z = a.z - b.z;
+        b.w = a.w - b.w;
+        y[off + i] = b;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -337,23 +383,28 @@ __global__ void ks_solve_kernel(int N, int m, const double2 *H, const double2 *g
 }
 
 // ---- launchers --------------------------------------------------------------------
-static inline int bblocks(const Geom &g, int N)
+static inline int bblocks(long long maxlen, int N)
 {
-    const int b = reduction_blocks(g) / (N < 4 ? N : 4);
-    return b < 16 ? 16 : b;
+    // about 4 blocks per SM over the whole batch, at least 16 per system, and no
+    // more than the longest field needs
+    long long b = (4LL * 152 + N - 1) / N;
+    if (b < 16) b = 16;
+    const long long need = (maxlen + BT - 1) / BT;
+    return (int)(b < need ? b : need < 1 ? 1 : need);
 }
 
-void bdot(const Exec &e, const void *V, long long vjs, int nv, const void *w, int N, BatchRed &br, int slot0)
+void bdot(const Exec &e, const Segs &S, const void *V, long long vjs, int nv, const void *w, int N, BatchRed &br,
+          int slot0)
 {
-    const long long n = 6 * e.g.stride;
     for (int j0 = 0; j0 < nv; j0 += 8) {
         const int nj = nv - j0 < 8 ? nv - j0 : 8;
-        Launch L_(e, K_DOT_F32, (double)N * e.g.Vh * 96.0 * (nj + 1), (double)N * e.g.Vh * 96 * nj);
+        Launch L_(e, K_DOT_F32, S.sites * 96.0 * (nj + 1), S.sites * 96 * nj);
         const float4 *Vj = (const float4 *)V + j0 * vjs;
         const dim3 grid(br.blocks, N);
 #define LQ_BDOT(NJ)                                                                                     \
     case NJ:                                                                                            \
-        bdot_kernel<NJ><<<grid, BT, 0, e.st>>>(Vj, vjs, n, (const float4 *)w, br.partial, br.pitch, slot0 + j0); \
+        bdot_kernel<NJ><<<grid, BT, 0, e.st>>>(Vj, vjs, S.seg, S.n, (const float4 *)w, br.partial, br.pitch, \
+                                               slot0 + j0);                                             \
         break;
         switch (nj) {
             LQ_BDOT(1)
@@ -369,29 +420,28 @@ void bdot(const Exec &e, const void *V, long long vjs, int nv, const void *w, in
     }
 }
 
-void baxpy(const Exec &e, const void *V, long long vjs, int nv, const double *c, int cstride, int sign, void *y,
-           int N, BatchRed *br, int slot)
+void baxpy(const Exec &e, const Segs &S, const void *V, long long vjs, int nv, const double *c, int cstride,
+           int sign, void *y, int N, BatchRed *br, int slot)
 {
-    Launch L_(e, K_AXPY_F32, (double)N * e.g.Vh * 96.0 * (nv + 2), (double)N * e.g.Vh * 96 * nv);
-    const long long n = 6 * e.g.stride;
-    const int blocks = br ? br->blocks : bblocks(e.g, N);
+    Launch L_(e, K_AXPY_F32, S.sites * 96.0 * (nv + 2), S.sites * 96 * nv);
+    const int blocks = br ? br->blocks : S.blocks;
     const dim3 grid(blocks, N);
     if (br)
-        baxpy_kernel<true><<<grid, BT, 0, e.st>>>((const float4 *)V, vjs, n, nv, (const double2 *)c, cstride,
-                                                  (float)sign, (float4 *)y, br->partial, br->pitch, slot);
+        baxpy_kernel<true><<<grid, BT, 0, e.st>>>((const float4 *)V, vjs, S.seg, S.n, nv, (const double2 *)c,
+                                                  cstride, (float)sign, (float4 *)y, br->partial, br->pitch, slot);
     else
-        baxpy_kernel<false><<<grid, BT, 0, e.st>>>((const float4 *)V, vjs, n, nv, (const double2 *)c, cstride,
-                                                   (float)sign, (float4 *)y, nullptr, 0, slot);
+        baxpy_kernel<false><<<grid, BT, 0, e.st>>>((const float4 *)V, vjs, S.seg, S.n, nv, (const double2 *)c,
+                                                   cstride, (float)sign, (float4 *)y, nullptr, 0, slot);
 }
 
-void bnorm(const Exec &e, int prec, const void *w, int N, BatchRed &br, int slot)
+void bnorm(const Exec &e, int prec, const Segs &S, const void *w, int N, BatchRed &br, int slot)
 {
-    Launch L_(e, K_NORM, (double)N * e.g.Vh * (prec == P32 ? 96.0 : 192.0));
+    Launch L_(e, K_NORM, S.sites * (prec == P32 ? 96.0 : 192.0));
     const dim3 grid(br.blocks, N);
     if (prec == P32)
-        bnorm_kernel<<<grid, BT, 0, e.st>>>((const float4 *)w, 6 * e.g.stride, br.partial, br.pitch, slot);
+        bnorm_kernel<<<grid, BT, 0, e.st>>>((const float4 *)w, S.seg, S.n, br.partial, br.pitch, slot);
     else
-        bnorm_df_kernel<<<grid, BT, 0, e.st>>>((const df2 *)w, 12 * e.g.stride, br.partial, br.pitch, slot);
+        bnorm_df_kernel<<<grid, BT, 0, e.st>>>((const df2 *)w, S.seg, S.n, br.partial, br.pitch, slot);
 }
 
 void bfinish(const Exec &e, BatchRed &br, int N, int first, int count)
@@ -402,11 +452,16 @@ void bfinish(const Exec &e, BatchRed &br, int N, int first, int count)
                                                         br.pitch);
 }
 
-void bscale(const Exec &e, const void *x, const double *s, void *y, int N)
+void bscale(const Exec &e, const Segs &S, const void *x, const double *s, void *y, int N)
 {
-    Launch L_(e, K_AXPY_F32, (double)N * e.g.Vh * 192.0);
-    const long long n = 6 * e.g.stride;
-    bscale_kernel<<<dim3((unsigned)((n + BT - 1) / BT), N), BT, 0, e.st>>>((const float4 *)x, n, s, (float4 *)y);
+    Launch L_(e, K_AXPY_F32, S.sites * 192.0);
+    bscale_kernel<<<dim3(S.blocks, N), BT, 0, e.st>>>((const float4 *)x, S.seg, S.n, s, (float4 *)y);
+}
+
+void bxmy(const Exec &e, const Segs &S, const void *x, void *y, int N)
+{
+    Launch L_(e, K_AXPY_F32, S.sites * 288.0, S.sites * 24.0);
+    bxmy_kernel<<<dim3(S.blocks, N), BT, 0, e.st>>>((const float4 *)x, S.seg, S.n, (float4 *)y);
 }
 
 void ks_init(const Exec &e, const KState &k, const double *nrm2, int nstride)
@@ -429,6 +484,6 @@ void ks_solve(const Exec &e, const KState &k)
     ks_solve_kernel<<<(k.N + 31) / 32, 32, 0, e.st>>>(k.N, k.m, k.H, k.g, k.kused, k.y, k.m);
 }
 
-int batch_blocks(const Geom &g, int N) { return bblocks(g, N); }
+int batch_blocks(long long maxlen, int N) { return bblocks(maxlen, N); }
 
 }  // namespace lq

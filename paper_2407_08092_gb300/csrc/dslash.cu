@@ -21,9 +21,8 @@
 
 namespace lq {
 
-#ifndef LQ_HOP_THREADS
 #define LQ_HOP_THREADS 128
-#endif
+static_assert(LQ_HOP_THREADS == kHopBlock, "hopping block size");
 
 // half spinor h[hs*3 + a] from the full spinor p[s*3 + a]; SIGN = -1 projects
 // with (1 - g_mu) (forward hop), SIGN = +1 with (1 + g_mu) (backward hop)
@@ -231,6 +230,31 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel_multi(Geom g, HopAr
     const long long o = r * k.fs;
     hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in + o, k.in2 ? k.in2 + o : nullptr,
                       k.b ? k.b + o : nullptr, k.out + o, s, c);
+}
+
+// The batched hop over the right-hand sides of several lattices of different
+// sizes in one persistent launch: each block walks the work table, an entry
+// naming a lattice, a block of blockDim.x consecutive sites and the first of
+// blockDim.y right-hand sides.  Entries of the same sites follow one another, so
+// a site's links and clover block reach L1/L2 once for all its right-hand sides.
+template <int MODE>
+__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_group_kernel(const LatDesc *__restrict__ d,
+                                                                   const int4 *__restrict__ tiles, int ntiles,
+                                                                   const float4 *in, const float4 *in2, float4 *out)
+{
+    constexpr int pout = MODE == HOP_K1 ? 1 : 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 w = __ldg(tiles + t);
+        const LatDesc *L = d + w.x;
+        const Geom g = L->g;
+        const long long s = (long long)w.y * blockDim.x + threadIdx.x;
+        const int r = w.z + threadIdx.y;
+        if (s >= g.Vh || r >= L->nrhs) continue;
+        const Coords c = cb_coords(g, s, pout);
+        const long long o = L->off + r * L->fs;
+        hop_body<float, MODE>(g, L->U[pout], L->U[1 - pout], L->clov[pout], 0.0f, in + o,
+                              in2 ? in2 + o : nullptr, nullptr, out + o, s, c);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -459,6 +483,37 @@ static int hop_class(int mode, int prec)
     return K_HOP_OTHER;
 }
 
+// algorithmic flops per site: 1320 for the eight hops (projection 12, two
+// SU(3) mat-vecs 132, accumulation 24, per direction, less the first
+// accumulation), 552 per clover-block pair, 24 per spinor add / scale
+static const double c_hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
+                                      1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552};
+
+double hop_bytes(int mode, int prec, int nrhs, double sites) { return sites * hop_site_bytes(mode, prec, nrhs); }
+double hop_flops(int mode, double site_rhs) { return site_rhs * c_hop_flops[mode]; }
+
+int hop_group_resident()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_group_kernel<HOP_K1>, LQ_HOP_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_group_kernel<HOP_K2>, LQ_HOP_THREADS, 0);
+    const int r = a < b ? a : b;
+    return r < 1 ? 1 : r;
+}
+
+void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, int ntiles, int grid, int spt,
+               const void *in, const void *in2, void *out, double bytes, double flops)
+{
+    Launch L_(e, mode == HOP_K1 ? K_HOP_K1_F32 : K_HOP_K2_F32, bytes, flops);
+    const dim3 block(spt, LQ_HOP_THREADS / spt);
+    if (mode == HOP_K1)
+        hop_group_kernel<HOP_K1><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, (const float4 *)in,
+                                                            (const float4 *)in2, (float4 *)out);
+    else
+        hop_group_kernel<HOP_K2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, (const float4 *)in,
+                                                            (const float4 *)in2, (float4 *)out);
+}
+
 void hop(const Exec &e, const HopCall &c)
 {
 #define LQ_CASE(M)                                                              \
@@ -467,13 +522,8 @@ void hop(const Exec &e, const HopCall &c)
         else if (c.prec == P32) launch_hop<float, M>(e, c);                     \
         else launch_hop<df64, M>(e, c);                                         \
         break;
-    // algorithmic flops per site: 1320 for the eight hops (projection 12,
-    // two SU(3) mat-vecs 132, accumulation 24, per direction, less the first
-    // accumulation), 552 per clover-block pair, 24 per spinor add / scale
-    static const double hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
-                                        1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552};
     Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec, c.nrhs),
-              (double)e.g.Vh * hop_flops[c.mode] * c.nrhs);
+              (double)e.g.Vh * c_hop_flops[c.mode] * c.nrhs);
     switch (c.mode) {
         LQ_CASE(HOP_K1)
         LQ_CASE(HOP_K2)

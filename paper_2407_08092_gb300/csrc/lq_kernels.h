@@ -138,6 +138,32 @@ struct HopCall {
     int nrhs = 1;          // right-hand sides: in, in2, b, out are nrhs consecutive fields
 };
 void hop(const Exec &e, const HopCall &c);
+
+// One member lattice of a batched solve over lattices of different sizes: its
+// geometry, FP32 links and clover, and where its right-hand sides' fields sit
+// in a multi-field (nrhs consecutive fields of fs vectors from `off`).
+struct LatDesc {
+    Geom g;
+    const float4 *U[2];      // 12-real FP32 links of both parities
+    const float4 *clov[2];   // clov[1]: C^{-1} of the odd sites (K1); clov[0]: C of the even sites (K2)
+    long long off;           // float4 vectors
+    long long fs;            // float4 vectors per field (6 * stride)
+    int nrhs;
+};
+// threads per block of the hopping kernels
+constexpr int kHopBlock = 128;
+// resident blocks per SM of the batched hopping kernel (for a persistent grid)
+int hop_group_resident();
+// One work-table entry of the batched hopping launch: lattice, site block (of
+// blockDim.x sites) and first right-hand side (of blockDim.y).
+// A persistent grid of `grid` blocks of (spt, kHopBlock / spt) threads
+// walks the table; mode HOP_K1 (odd output) or HOP_K2 (even output), FP32.
+void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, int ntiles, int grid, int spt,
+               const void *in, const void *in2, void *out, double bytes, double flops);
+// FP32 hopping-launch byte and flop counts of `sites` output sites with nrhs
+// right-hand sides sharing links and clover
+double hop_bytes(int mode, int prec, int nrhs, double sites);
+double hop_flops(int mode, double site_rhs);
 // out = C in (site-diagonal apply of packed blocks of one parity)
 void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void *out);
 
@@ -197,16 +223,29 @@ struct KState {
     double *est;      // [N] residual estimate |g_{k+1}|
     double *target;   // [N] absolute residual target of the cycle
 };
-// FP32 batched BLAS; basis vector j of right-hand side r at V + j * vjs + r * n vectors
-void bdot(const Exec &e, const void *V, long long vjs, int nv, const void *w, int N, BatchRed &br, int slot0);
-void baxpy(const Exec &e, const void *V, long long vjs, int nv, const double *c, int cstride, int sign, void *y,
-           int N, BatchRed *br, int slot);
-void bnorm(const Exec &e, int prec, const void *w, int N, BatchRed &br, int slot);   // P32 or PDF
+// The systems of a batch inside one buffer (a multi-field): system r's field
+// is vectors [off_r, off_r + len_r) (16-byte vectors); seg holds {off, len} per
+// system in device memory, or is null for the uniform layout off_r = r * n,
+// len_r = n.  blocks: grid of the non-reducing kernels per system; sites: the
+// systems' sites of one parity in total (byte accounting).
+struct Segs {
+    const longlong2 *seg = nullptr;
+    long long n = 0;
+    int blocks = 1;
+    double sites = 0.0;
+};
+// FP32 batched BLAS; basis vector j of system r at V + j * vjs + off_r
+void bdot(const Exec &e, const Segs &S, const void *V, long long vjs, int nv, const void *w, int N, BatchRed &br,
+          int slot0);
+void baxpy(const Exec &e, const Segs &S, const void *V, long long vjs, int nv, const double *c, int cstride,
+           int sign, void *y, int N, BatchRed *br, int slot);
+void bnorm(const Exec &e, int prec, const Segs &S, const void *w, int N, BatchRed &br, int slot);   // P32 or PDF
 void bfinish(const Exec &e, BatchRed &br, int N, int first, int count);
-void bscale(const Exec &e, const void *x, const double *s, void *y, int N);
+void bscale(const Exec &e, const Segs &S, const void *x, const double *s, void *y, int N);
+void bxmy(const Exec &e, const Segs &S, const void *x, void *y, int N);   // y = x - y
 void ks_init(const Exec &e, const KState &k, const double *nrm2, int nstride);
 void ks_step(const Exec &e, const KState &k, int step, int passes, const double *dots, int dstride);
 void ks_solve(const Exec &e, const KState &k);
-int batch_blocks(const Geom &g, int N);
+int batch_blocks(long long maxlen, int N);   // reduction blocks per system
 
 }  // namespace lq

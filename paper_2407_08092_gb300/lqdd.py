@@ -251,6 +251,63 @@ def lq_fermion_force(ctx, params: lq_solver_params, phi, G):
     return s, S.value, list(st)
 
 
+_lib.lq_group_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P]
+_lib.lq_group_create.restype = ctypes.c_int
+_lib.lq_group_destroy.argtypes = [_P]
+_lib.lq_group_destroy.restype = ctypes.c_int
+_lib.lq_solve_group.argtypes = [_P, ctypes.POINTER(lq_solver_params), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(lq_stats)]
+_lib.lq_solve_group.restype = ctypes.c_int
+_lib.lq_group_set_autotune.argtypes = [_P, ctypes.c_int]
+_lib.lq_group_set_autotune.restype = ctypes.c_int
+_lib.lq_group_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+_lib.lq_group_tuning.restype = ctypes.c_int
+
+
+def lq_group_create(members, stream: int | None = None):
+    """A group of contexts solved together; errors are reported through the
+    first member's lq_last_error."""
+    arr = (_P * len(members))(*[m.value if isinstance(m, _P) else m for m in members])
+    grp = _P()
+    _check(members[0], _lib.lq_group_create(ctypes.byref(grp), arr, len(members), _P(stream or 0)))
+    return grp
+
+
+def lq_group_destroy(grp) -> None:
+    _check(None, _lib.lq_group_destroy(grp))
+
+
+def lq_solve_group(grp, first_member, params: lq_solver_params, b_list, x_list):
+    """Solve every member's right-hand sides together.  b_list[l], x_list[l]:
+    [n_rhs_l, V_l, 4, 3] complex128 CUDA tensors.  Returns (status, [stats per
+    system, member by member]); raises on every status but OK and NOT_CONVERGED
+    (the message comes from `first_member`, the group's first context)."""
+    M = len(b_list)
+    n = (ctypes.c_int * M)(*[int(b.shape[0]) for b in b_list])
+    bp = (_P * M)(*[_ptr(b) for b in b_list])
+    xp = (_P * M)(*[_ptr(x) for x in x_list])
+    st = (lq_stats * sum(n))()
+    s = _lib.lq_solve_group(grp, ctypes.byref(params), n, bp, xp, st)
+    if s not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(first_member, s)
+    return s, list(st)
+
+
+def lq_group_set_autotune(grp, on: bool) -> None:
+    _check(None, _lib.lq_group_set_autotune(grp, int(bool(on))))
+
+
+def lq_group_tuning(grp):
+    """(sites per tile, grid, BLAS blocks per system, hop ms, BLAS ms) in use."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    d, e = ctypes.c_double(), ctypes.c_double()
+    _check(None, _lib.lq_group_tuning(grp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                      ctypes.byref(e)))
+    return a.value, b.value, c.value, d.value, e.value
+
+
 def make_batch_params(tol=1e-10, restart=16, max_restarts=10, smooth_n=8, smooth_tol=1e-5) -> lq_solver_params:
     """Parameters of lq_solve_batch: df64 defect correction around batched FP32 GMRES(restart)."""
     return make_params(solver=LQ_SOLVER_GMRES, prec=LQ_DF64, tol=tol, restart=restart, max_restarts=max_restarts,

@@ -101,3 +101,76 @@ def test_solve_batch_status_codes():
         assert ei.value.status == lqdd.LQ_ERR_NAN
     finally:
         p.close()
+
+
+def test_solve_group_uneven_lattices():
+    """Right-hand sides of four lattices of different sizes (each with its own
+    links) solved together: every system meets the target on the oracle's true
+    residual, and the launch shapes the autotuner chose are valid; with the
+    autotuner off the fixed shapes give converged solutions as well."""
+    from paper_2407_08092_gb300 import lqdd
+    specs = [((8, 8, 8, 8), 3), ((6, 4, 2, 4), 2), ((4, 4, 4, 4), 4), ((16, 8, 8, 8), 2)]
+    pairs = [Pair(L, eps=0.25, seed=1101 + i, m0=0.05, csw=1.0) for i, (L, _) in enumerate(specs)]
+    grp = lqdd.lq_group_create([p.ctx for p in pairs], pairs[0].torch.cuda.current_stream().cuda_stream)
+    try:
+        bs = [sources(p.lat, n, 400 + 10 * i) for i, (p, (_, n)) in enumerate(zip(pairs, specs))]
+        db = [p.dev(b) for p, b in zip(pairs, bs)]
+        for autotune in (True, False):
+            lqdd.lq_group_set_autotune(grp, autotune)
+            xs = [p.torch.zeros_like(d) for p, d in zip(pairs, db)]
+            status, stats = lqdd.lq_solve_group(grp, pairs[0].ctx, lqdd.make_batch_params(tol=1e-10, restart=16),
+                                                db, xs)
+            assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
+            assert len(stats) == sum(n for _, n in specs)
+            k = 0
+            for p, b, x in zip(pairs, bs, xs):
+                xh = p.host(x)
+                for r in range(b.shape[0]):
+                    r_true = np.linalg.norm(b[r] - p.lat.dirac(xh[r])) / np.linalg.norm(b[r])
+                    assert r_true <= 2e-10, (p.L, r, r_true)
+                    assert abs(r_true - stats[k].rel_resid_true) <= 1e-3 * r_true + 1e-15
+                    k += 1
+            spt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
+            assert spt in (16, 32, 64, 128) and grid >= 1 and blas >= 1
+            if autotune:
+                assert hop_ms > 0 and blas_ms > 0
+            else:
+                assert (spt, hop_ms, blas_ms) == (32, 0.0, 0.0)
+        # the same systems one member at a time (lq_solve_batch) give the same solutions
+        for p, d, x in zip(pairs, db, xs):
+            x1 = p.torch.zeros_like(d)
+            status, _ = lqdd.lq_solve_batch(p.ctx, lqdd.make_batch_params(tol=1e-10, restart=16), d.shape[0], d, x1)
+            assert status == lqdd.LQ_OK
+            assert rel(p.host(x1), p.host(x)) < 1e-8
+    finally:
+        lqdd.lq_group_destroy(grp)
+        for p in pairs:
+            p.close()
+
+
+def test_solve_group_status_codes():
+    from paper_2407_08092_gb300 import lqdd
+    a = Pair((4, 4, 4, 4), seed=7)
+    b = Pair((6, 4, 2, 4), seed=8)
+    try:
+        with pytest.raises(lqdd.LqError):
+            lqdd.lq_group_create([a.ctx, a.ctx])            # a context twice
+        grp = lqdd.lq_group_create([a.ctx, b.ctx])
+        try:
+            with pytest.raises(lqdd.LqError):
+                lqdd.lq_group_tuning(grp)                   # no solve yet
+            da = a.dev(sources(a.lat, 2, 11))
+            dbb = b.dev(sources(b.lat, 1, 12))
+            xa, xb = a.torch.zeros_like(da), b.torch.zeros_like(dbb)
+            with pytest.raises(lqdd.LqError) as ei:          # the batch runs in df64 / FP32 only
+                lqdd.lq_solve_group(grp, a.ctx, lqdd.make_params(tol=1e-10), [da, dbb], [xa, xb])
+            assert ei.value.status == lqdd.LQ_ERR_ARG
+            status, stats = lqdd.lq_solve_group(grp, a.ctx, lqdd.make_batch_params(tol=1e-13, max_restarts=1,
+                                                                                     smooth_n=1),
+                                                [da, dbb], [xa, xb])
+            assert status == lqdd.LQ_ERR_NOT_CONVERGED and len(stats) == 3
+        finally:
+            lqdd.lq_group_destroy(grp)
+    finally:
+        a.close()
+        b.close()
