@@ -23,6 +23,15 @@ namespace lq {
 
 #define LQ_HOP_THREADS 128
 static_assert(LQ_HOP_THREADS == kHopBlock, "hopping block size");
+// minimum resident blocks per SM asked of the single-right-hand-side kernels.
+// Unset leaves the register allocation to the compiler's default for
+// 128-thread blocks, which differs from an explicit 1 (that one lets the
+// kernels grow to about 160 registers).
+#ifdef LQ_HOP_MINB
+#define LQ_HOP_BOUNDS __launch_bounds__(LQ_HOP_THREADS, LQ_HOP_MINB)
+#else
+#define LQ_HOP_BOUNDS __launch_bounds__(LQ_HOP_THREADS)
+#endif
 
 // half spinor h[hs*3 + a] from the full spinor p[s*3 + a]; SIGN = -1 projects
 // with (1 - g_mu) (forward hop), SIGN = +1 with (1 + g_mu) (backward hop)
@@ -207,7 +216,20 @@ __device__ __forceinline__ void hop_body(const Geom &g, const typename St<R>::ve
 // and from the caches for the other right-hand sides; it is a separate
 // instantiation so that the single right-hand-side kernel keeps its registers.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel(Geom g, HopArgs<R> k)
+__global__ void LQ_HOP_BOUNDS hop_kernel(Geom g, HopArgs<R> k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+}
+
+// The same for FP32 K2 and its Richardson form, asked to fit six blocks per SM
+// (80 registers, a few bytes of spills): measured on GB300 on 32^3 x 64, K2
+// moves from 0.89 to 0.93 of the copy bandwidth this way, while K1 (78
+// registers unbounded) gains nothing.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(LQ_HOP_THREADS, 6) hop_kernel_occ(Geom g, HopArgs<R> k)
 {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
@@ -237,8 +259,13 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel_multi(Geom g, HopAr
 // naming a lattice, a block of blockDim.x consecutive sites and the first of
 // blockDim.y right-hand sides.  Entries of the same sites follow one another, so
 // a site's links and clover block reach L1/L2 once for all its right-hand sides.
+#ifdef LQ_GROUP_MINB
+#define LQ_GROUP_BOUNDS __launch_bounds__(LQ_HOP_THREADS, LQ_GROUP_MINB)
+#else
+#define LQ_GROUP_BOUNDS __launch_bounds__(LQ_HOP_THREADS)
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_group_kernel(const LatDesc *__restrict__ d,
+__global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
                                                                    const int4 *__restrict__ tiles, int ntiles,
                                                                    const float4 *in, const float4 *in2, float4 *out)
 {
@@ -454,7 +481,12 @@ static void launch_hop(const Exec &e, const HopCall &c)
         hop_kernel_multi<R, MODE><<<(unsigned)(sblocks * groups), dim3(32, rpb), 0, e.st>>>(e.g, k);
     }
     else
-        hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+    {
+        if constexpr (std::is_same<R, float>::value && (MODE == HOP_K2 || MODE == HOP_RICH))
+            hop_kernel_occ<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+        else
+            hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+    }
 }
 
 // algorithmic bytes per output site of one hopping launch (FP64 and df64 share

@@ -3,8 +3,10 @@
 Builds a context on a seeded lattice (default 24^3 x 48, whose per-launch
 working set is larger than L2 but whose device footprint stays within a few
 GB) and then either applies D_S (K1 + K2) `--apps` times in one precision
-through the C ABI, or runs `--apps` mixed-precision solves (FGMRES(10) in
-df64 preconditioned by GMRES(16) in FP32), e.g.
+through the C ABI (printing per-class device times), runs `--apps`
+mixed-precision solves (FGMRES(10) in df64 preconditioned by GMRES(16) in
+FP32), a batched solve of `--nrhs` point sources through a one-member group
+(printing the autotuner's choice), or the fermion-force kernel, e.g.
 ``python -m paper_2407_08092_gb300.profile_case --lattice 24,24,24,48 --prec 1 --apps 3``.
 """
 import argparse
@@ -32,8 +34,17 @@ def main():
         n = V if a.op == lqdd.LQ_OP_FULL else V // 2
         x = torch.from_numpy(synth.gaussian_spinor(n, 2003)).cuda()
         y = torch.empty_like(x)
+        lqdd.lq_apply(ctx, a.op, a.prec, x, y)
+        lqdd.lq_profile(ctx, 1)
         for _ in range(a.apps):
             lqdd.lq_apply(ctx, a.op, a.prec, x, y)
+        torch.cuda.synchronize()
+        for c in range(lqdd.LQ_K_COUNT):
+            nl, ms, by, fl = lqdd.lq_profile_read(ctx, c)
+            if nl:
+                print(f"{lqdd.lq_kernel_class_name(c):14s} {nl:5d} launches {1e3 * ms / nl:9.2f} us/launch "
+                      f"{by / (ms * 1e6):8.1f} GB/s")
+        lqdd.lq_profile(ctx, 0)
         out = float(y.abs().sum())
     elif a.mode == "batch":
         n = a.nrhs
@@ -41,13 +52,16 @@ def main():
         for r in range(n):
             b[r, 0, r % 4, (r // 4) % 3] = 1.0
         x = torch.zeros_like(b)
+        grp = lqdd.lq_group_create([ctx], torch.cuda.current_stream().cuda_stream)
         for _ in range(a.apps):
             x.zero_()
-            status, st = lqdd.lq_solve_batch(ctx, lqdd.make_batch_params(), n, b, x)
+            status, st = lqdd.lq_solve_group(grp, ctx, lqdd.make_batch_params(), [b], [x])
             assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
         out = max(s.rel_resid_true for s in st)
         print("outer corrections", [s.iters for s in st], "inner steps", [s.inner_iters for s in st],
               "ms", round(st[0].time_ms, 2))
+        print("tuning (sites/tile, grid, blas blocks, hop pair ms, blas pair ms)", lqdd.lq_group_tuning(grp))
+        lqdd.lq_group_destroy(grp)
     elif a.mode == "force":
         X = torch.from_numpy(synth.gaussian_spinor(V, 71)).cuda()
         Y = torch.from_numpy(synth.gaussian_spinor(V, 72)).cuda()
