@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-force", action="store_true")
+    ap.add_argument("--no-sap", action="store_true")
     return ap.parse_args()
 
 
@@ -324,6 +325,48 @@ def run_batched(lqdd, synth, torch, stream, dev):
             lqdd.lq_destroy(ctx)
 
 
+def run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks, V, omega):
+    """SAP(3, 4) and Richardson(5) smoother calls (medians of 5) and the FGMRES(10)
+    df64 solve to 1e-10 preconditioned by SAP(3, 4), on the benchmark lattice."""
+    sap = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_SAP, smooth_n=3, smooth_m=4, inner_prec=lqdd.LQ_F32,
+                           prec=lqdd.LQ_DF64)
+    rich = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=omega, inner_prec=lqdd.LQ_F32,
+                            prec=lqdd.LQ_DF64)
+    solve = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_SAP, smooth_n=3, smooth_m=4,
+                             inner_prec=lqdd.LQ_F32)
+    e = torch.empty_like(db)
+
+    def med(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            z.record(stream)
+            torch.cuda.synchronize()
+            ts.append((a.elapsed_time(z), out))
+        return sorted(ts, key=lambda t: t[0])[len(ts) // 2]
+
+    lqdd.lq_profile(ctx, 1)
+    t_sap, _ = med(lambda: lqdd.lq_smooth(ctx, sap, db, e))
+    prof = read_profile(lqdd, ctx)
+    lqdd.lq_profile(ctx, 0)
+    t_rich, _ = med(lambda: lqdd.lq_smooth(ctx, rich, db, e))
+
+    def solve_once():
+        x.zero_()
+        return lqdd.lq_solve(ctx, solve, db, x)
+    t_solve, (status, st) = med(solve_once, reps=3)
+    res = {"sap_3_4_ms": round(t_sap, 3), "richardson_5_ms": round(t_rich, 3), "blocks": [4, 4, 4, 4],
+           "fgmres_sap_ms": round(t_solve, 2), "fgmres_sap": st.as_dict(), "status": lqdd.lq_status_string(status)}
+    if "sap" in prof:
+        res["roofline"] = roofline_of("sap", prof["sap"], pk_peaks, V)
+    return res
+
+
 def read_profile(lqdd, ctx):
     """Per-class launches, device ms, algorithmic bytes and flops since lq_profile(ctx, 1)."""
     prof = {}
@@ -480,9 +523,14 @@ def run_ours(args):
             runs.append((a.elapsed_time(z), st.as_dict(), lqdd.lq_status_string(status)))
         times[name] = sorted(runs, key=lambda r: r[0])[2]          # median of 5
 
-    # batched: the 12 spin-colour point sources of one propagator on 24^3 x 48
-    # (eps 0.25, m0 0.05, link seed 1103), one lq_solve_batch call against 12
-    # single mixed solves of the same systems
+    # smoothers on the benchmark lattice: one SAP(3, 4) call (the paper's Table 2
+    # smoother call; 4^4 blocks, FP32) against one odd-even Richardson(5) call,
+    # and the FGMRES solve preconditioned by SAP(3, 4) against the mixed solve
+    sap = None
+    if not args.no_sap:
+        sap = run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks=peaks(), V=V, omega=info["omega"])
+
+    # batched: 12 spin-colour point sources on each of four lattices
     batched = None
     if not args.no_batch:
         batched = run_batched(lqdd, synth, torch, stream, dev)
@@ -571,6 +619,7 @@ def run_ours(args):
                   "status": {k: times[k][2] for k in times}},
         "batched": batched,
         "force": force,
+        "sap": sap,
         "kernels": prof,
         "step_bytes": step_bytes,
     }

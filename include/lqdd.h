@@ -76,7 +76,7 @@ typedef enum {
 } lq_op;
 
 typedef enum { LQ_SOLVER_GMRES = 0, LQ_SOLVER_FGMRES = 1 } lq_solver_kind;
-typedef enum { LQ_SMOOTH_NONE = 0, LQ_SMOOTH_RICHARDSON = 1, LQ_SMOOTH_GMRES = 2 } lq_smoother_kind;
+typedef enum { LQ_SMOOTH_NONE = 0, LQ_SMOOTH_RICHARDSON = 1, LQ_SMOOTH_GMRES = 2, LQ_SMOOTH_SAP = 3 } lq_smoother_kind;
 
 typedef struct {
     int L[4];      /* Lx, Ly, Lz, Lt: even, >= 2 */
@@ -97,12 +97,15 @@ typedef struct {
     int restart;         /* Krylov length m of each cycle, 1..256 */
     int max_restarts;    /* maximum number of cycles, >= 1 */
     int smoother;        /* lq_smoother_kind: preconditioner of FGMRES, or the method of lq_smooth */
-    int smooth_n;        /* Richardson sweeps n, or GMRES(n, m) cycles n */
-    int smooth_m;        /* GMRES(n, m) cycle length m, 1..256 */
+    int smooth_n;        /* Richardson sweeps n, GMRES(n, m) cycles n, or SAP(n, m) iterations n */
+    int smooth_m;        /* GMRES(n, m) cycle length m, 1..256, or SAP(n, m) Minimal Residual steps m */
     double omega;        /* Richardson weight omega = delta / |lambda_max(D_S)| (Algorithm 4) */
     double smooth_tol;   /* GMRES smoother: also stop once its relative residual <= smooth_tol
                             (0 runs exactly n cycles of m steps) */
-    int inner_prec;      /* lq_prec of the smoother / preconditioner */
+    int inner_prec;      /* lq_prec of the smoother / preconditioner (LQ_F32 for SAP) */
+    int sap_block[4];    /* SAP: block extents (even, dividing the lattice, with an even number of
+                            blocks or one along each direction, at most 256 sites); zeros select
+                            4 along every direction that allows it */
 } lq_solver_params;
 
 typedef struct {
@@ -156,10 +159,16 @@ lq_status lq_estimate_norm(lq_ctx *ctx, int prec, int iters, const void *v0, dou
  * Deterministic two-stage FP64 reduction.  Synchronises. */
 lq_status lq_norm2(lq_ctx *ctx, const void *v, long long n_sites, double *out);
 
-/* The odd-even smoother e = M_n r of Sec. 2.4.5 / Fig. 1: Eq. 2 with D_S^{-1}
- * replaced by `smooth_n` Richardson sweeps (weight omega, Algorithm 4) or by
- * GMRES(smooth_n, smooth_m) (Algorithm 2), started from zero, run in
- * params->inner_prec.  r, e: full spinors. */
+/* The smoother e = M r, started from zero, run in params->inner_prec.
+ * Richardson or GMRES: the odd-even smoother M_n of Sec. 2.4.5 / Fig. 1, i.e.
+ * Eq. 2 with D_S^{-1} replaced by `smooth_n` Richardson sweeps (weight omega,
+ * Algorithm 4) or by GMRES(smooth_n, smooth_m) (Algorithm 2).
+ * SAP: SAP(smooth_n, smooth_m) on the full lattice (Algorithm 1): red then black
+ * blocks of extents sap_block, each block solved by odd-even Minimal Residual
+ * with smooth_m steps (FP32; one launch per colour, one CTA per block).  As the
+ * FGMRES preconditioner of lq_solve, SAP is applied to (v_e, 0) and its even
+ * half taken (the even-even block of D^{-1} is D_S^{-1}).
+ * r, e: full spinors. */
 lq_status lq_smooth(lq_ctx *ctx, const lq_solver_params *params, const void *r, void *e);
 
 /* Solve D x = b by odd-even reduction (Eq. 2): prepare, solve the Schur system
@@ -281,6 +290,7 @@ typedef enum {
     LQ_K_DOT_DF64, LQ_K_AXPY_DF64,        /* BLAS-1 in df64 */
     LQ_K_CLOVER_FIELD,   /* field strengths F_munu of the six planes from the leaves (df64) */
     LQ_K_FORCE,          /* fermion force: clover insertion and per-link gradient (df64) */
+    LQ_K_SAP,            /* SAP block solves (FP32) */
     LQ_K_COUNT
 } lq_kernel_class;
 

@@ -17,6 +17,7 @@
 //  * The odd-even smoother M_n (Sec. 2.4.5): prepare, smoother on D_S,
 //    reconstruct (Eq. 2).
 //  * Power iteration on D_S^+ D_S for ||D_S||_2 (Sec. 2.4.4).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -61,6 +62,9 @@ struct lq_ctx {
     std::string err;
     Prof prof;
     lq_group *self_group = nullptr;   // the one-member group behind lq_solve_batch
+    int sap_b[4] = {0, 0, 0, 0};      // block extents of the SAP origin tables below
+    int4 *sap_origin[2] = {nullptr, nullptr};
+    int sap_count[2] = {0, 0};
     Exec ex() { return Exec{g, st, &ctr, &prof}; }
 };
 
@@ -462,9 +466,98 @@ void richardson(lq_ctx *c, int prec, const void *b, void *x, int n, double omega
     for (int i = 1; i < n; i++) op_rich_sweep(c, prec, x, b, omega, t);
 }
 
+// ---- SAP(n, m), Algorithm 1 ------------------------------------------------------
+
+// block extents of the SAP decomposition: params->sap_block, or 4 along every
+// direction that allows it (and the whole extent of a direction of length 2)
+void sap_dims(lq_ctx *c, const lq_solver_params *p, int b[4])
+{
+    const int *L = c->lat.L;
+    for (int mu = 0; mu < 4; mu++) {
+        int v = p->sap_block[mu];
+        if (v == 0) v = (L[mu] % 4 == 0 && (L[mu] / 4 == 1 || (L[mu] / 4) % 2 == 0)) ? 4 : (L[mu] == 2 ? 2 : -1);
+        if (v < 2 || v % 2 || L[mu] % v) fail(c, LQ_ERR_ARG, "SAP block extents must be even and divide the lattice");
+        const int n = L[mu] / v;
+        if (n != 1 && n % 2) fail(c, LQ_ERR_ARG, "SAP needs an even number of blocks (or one) along each direction");
+        b[mu] = v;
+    }
+    if ((long long)b[0] * b[1] * b[2] * b[3] > 256) fail(c, LQ_ERR_ARG, "SAP blocks hold at most 256 sites");
+}
+
+// the first site of every block of each colour (colour = parity of the block
+// coordinates' sum), rebuilt when the block extents change
+void sap_tables(lq_ctx *c, const int b[4])
+{
+    if (c->sap_origin[0] && std::equal(b, b + 4, c->sap_b)) return;
+    const int *L = c->lat.L;
+    std::vector<int4> org[2];
+    for (int t = 0; t < L[3] / b[3]; t++)
+        for (int z = 0; z < L[2] / b[2]; z++)
+            for (int y = 0; y < L[1] / b[1]; y++)
+                for (int x = 0; x < L[0] / b[0]; x++)
+                    org[(x + y + z + t) & 1].push_back(make_int4(x * b[0], y * b[1], z * b[2], t * b[3]));
+    for (int col = 0; col < 2; col++) {
+        const size_t bytes = sizeof(int4) * (org[col].size() ? org[col].size() : 1);
+        c->sap_origin[col] = (int4 *)ws(c, col ? "sap:org1" : "sap:org0", bytes);
+        if (!org[col].empty())
+            ck(c, cudaMemcpy(c->sap_origin[col], org[col].data(), sizeof(int4) * org[col].size(),
+                             cudaMemcpyHostToDevice),
+               "cudaMemcpy H2D");
+        c->sap_count[col] = (int)org[col].size();
+    }
+    std::copy(b, b + 4, c->sap_b);
+}
+
+// x = SAP(n, m) b from x = 0 on the full lattice, FP32 internal fields
+void sap_apply(lq_ctx *c, const lq_solver_params *p, const void *be, const void *bo, void *xe, void *xo)
+{
+    int b[4];
+    sap_dims(c, p, b);
+    sap_tables(c, b);
+    Exec e = c->ex();
+    zero(e, P32, xe);
+    zero(e, P32, xo);
+    void *re = field(c, P32, "sap:re"), *ro = field(c, P32, "sap:ro");
+    SapLaunch L;
+    std::copy(b, b + 4, L.b);
+    L.U[0] = c->U32[0];
+    L.U[1] = c->U32[1];
+    L.Ce = c->C32[0];
+    L.Ci = c->Ci32;
+    L.x[0] = xe;
+    L.x[1] = xo;
+    L.m = p->smooth_m;
+    for (int i = 0; i < p->smooth_n; i++)
+        for (int col = 0; col < 2; col++) {
+            if (i == 0 && col == 0) {      // x = 0: r = b
+                L.r[0] = be;
+                L.r[1] = bo;
+            } else {                       // r = b - D x
+                op_full(c, P32, xe, xo, re, ro);
+                axpby(e, P32, 1.0, 0.0, be, -1.0, 0.0, re);
+                axpby(e, P32, 1.0, 0.0, bo, -1.0, 0.0, ro);
+                L.r[0] = re;
+                L.r[1] = ro;
+            }
+            L.origin = c->sap_origin[col];
+            L.count = c->sap_count[col];
+            sap_blocks(e, L);
+        }
+    ck_launch(c, "SAP");
+}
+
 // the preconditioner / smoother on D_S: z = M v, both in precision q
 long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void *v, void *z)
 {
+    if (p->smoother == LQ_SMOOTH_SAP) {
+        // the even half of SAP applied to (v, 0): D^{-1} restricted to the even
+        // sites is D_S^{-1}
+        if (q != P32) fail(c, LQ_ERR_ARG, "SAP runs in LQ_F32 (inner_prec)");
+        void *zo = field(c, P32, "sap:zo"), *vo = field(c, P32, "sap:vo");
+        zero(c->ex(), P32, vo);
+        sap_apply(c, p, v, vo, z, zo);
+        return p->smooth_n;
+    }
     if (p->smoother == LQ_SMOOTH_RICHARDSON) {
         richardson(c, q, v, z, p->smooth_n, p->omega, "rich");
         return p->smooth_n;
@@ -565,7 +658,9 @@ void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
         if (p->solver == LQ_SOLVER_FGMRES && p->prec == LQ_F32)
             fail(c, LQ_ERR_ARG, "the FGMRES outer iteration needs LQ_F64 or LQ_DF64");
     }
-    if (p->smoother < LQ_SMOOTH_NONE || p->smoother > LQ_SMOOTH_GMRES) fail(c, LQ_ERR_ARG, "bad smoother");
+    if (p->smoother < LQ_SMOOTH_NONE || p->smoother > LQ_SMOOTH_SAP) fail(c, LQ_ERR_ARG, "bad smoother");
+    if (p->smoother == LQ_SMOOTH_SAP && (p->inner_prec != LQ_F32 || p->smooth_m < 0))
+        fail(c, LQ_ERR_ARG, "SAP runs in LQ_F32 with smooth_m >= 0 Minimal Residual steps");
     if (!valid_prec(p->inner_prec)) fail(c, LQ_ERR_ARG, "bad inner_prec");
     if (p->smoother != LQ_SMOOTH_NONE && p->smooth_n < 0) fail(c, LQ_ERR_ARG, "smooth_n < 0");
     if (p->smoother == LQ_SMOOTH_GMRES && (p->smooth_m < 1 || p->smooth_m > MAX_RESTART))
@@ -1296,6 +1391,14 @@ lq_status lq_smooth(lq_ctx *c, const lq_solver_params *p, const void *r, void *e
         check_params(c, p, false);
         need_gauge(c);
         Exec e = c->ex();
+        if (p->smoother == LQ_SMOOTH_SAP) {   // Algorithm 1 on the full lattice
+            void *be = field(c, P32, "sm:be"), *bo = field(c, P32, "sm:bo");
+            void *xe = field(c, P32, "sm:xe"), *xo = field(c, P32, "sm:xo");
+            import_full(e, P32, r, be, bo);
+            sap_apply(c, p, be, bo, xe, xo);
+            export_full(e, P32, xe, xo, eo);
+            return;
+        }
         const int q = p->inner_prec;
         const int W = p->prec;
         if (W != LQ_F64 && W != LQ_DF64) fail(c, LQ_ERR_ARG, "prec (prepare/reconstruct) must be LQ_F64 or LQ_DF64");
@@ -1802,7 +1905,7 @@ const char *lq_kernel_class_name(int cls)
     static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
                                          "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
                                          "norm", "reduce_finish", "copy", "hop_k1_df64", "hop_k2_df64",
-                                         "dot_df64", "axpy_df64", "clover_field", "force"};
+                                         "dot_df64", "axpy_df64", "clover_field", "force", "sap"};
     return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 

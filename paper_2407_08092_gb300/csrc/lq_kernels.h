@@ -18,7 +18,7 @@ enum Prec { P64 = 0, P32 = 1, PDF = 2 };
 enum KClass {
     K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
     K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY,
-    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_FORCE, K_COUNT
+    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_FORCE, K_SAP, K_COUNT
 };
 
 // Optional CUDA-event timing of every launch (enabled by lq_profile).
@@ -103,6 +103,23 @@ void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag);
 void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32);
 // natural export: out[V][2][6][6] c128 from FP64 packed blocks (null parity pointer -> zeros)
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
+
+// ---- SAP block solves (sap.cu) ----------------------------------------------
+// One launch solves every block of one colour (FP32): for each block (origin
+// in lattice coordinates), odd-even Minimal Residual on the block operator
+// with m steps against the residual r, then x += e on the block's sites.
+struct SapLaunch {
+    int b[4];                 // block extents: even, dividing the lattice, b0 b1 b2 b3 <= 256
+    const int4 *origin;       // device: first site of each block of the colour
+    int count;                // blocks of the colour
+    const void *U[2];         // FP32 links by parity
+    const void *Ce;           // FP32 C of the even sites
+    const void *Ci;           // FP32 C^{-1} of the odd sites
+    const void *r[2];         // FP32 residual by parity
+    void *x[2];               // FP32 solution by parity (updated)
+    int m;
+};
+void sap_blocks(const Exec &e, const SapLaunch &s);
 
 // ---- fermion force (force.cu) ----------------------------------------------
 // X, Y: internal df64 full fields (even, odd).  Gam: device scratch of

@@ -1,0 +1,272 @@
+// The block solves of SAP(n, m), Algorithm 1 (Sec. 2.4.1), in FP32.
+//
+// One CTA owns one block of the decomposition and does its whole solve:
+//   r_hat_e = r_e - D_eo D_oo^{-1} r_o                  (odd-even inside the block,
+//   m steps of Minimal Residual on S = D_ee - D_eo D_oo^{-1} D_oe  Sec. 2.4.5)
+//   e_o = D_oo^{-1} (r_o - D_oe e_e)
+//   x += e on the block's sites
+// where every hop that leaves the block is dropped (the block operator is D
+// restricted to the block).  The blocks of one colour touch no other block of
+// that colour, so all of them run in one launch with no interaction; the MR
+// dot products are CTA-local reductions, so an MR step needs no grid-wide
+// synchronisation.  The block's MR residual and iterate and the odd
+// intermediate live in shared memory, where the hops read their neighbours;
+// links and clover blocks come from the global FP32 copies (L1/L2 after the
+// first sweep).
+#include "lq_kernels.h"
+#include "spin.cuh"
+
+namespace lq {
+
+static constexpr int SAP_THREADS = 128;   // one thread per block site of each parity
+
+struct SapArgs {
+    Geom g;
+    int b[4];                 // block extents (even, dividing the lattice)
+    int bvh;                  // sites of one parity in a block (<= SAP_THREADS)
+    const int4 *origin;       // lattice coordinates of the first site of each block of the colour
+    const float4 *U[2];       // FP32 links by parity
+    const float4 *Ce;         // C of the even sites
+    const float4 *Ci;         // C^{-1} of the odd sites
+    const float4 *r[2];       // residual by parity
+    float4 *x[2];             // solution by parity (updated)
+    int m;                    // Minimal Residual steps
+};
+
+// local coordinates of the i-th block site of parity p (lexicographic over
+// the block, the same checkerboard numbering as the lattice's)
+__device__ __forceinline__ void sap_local(const SapArgs &a, int i, int p, int l[4])
+{
+    const int bx2 = a.b[0] >> 1;
+    const int row = i / bx2;
+    l[1] = row % a.b[1];
+    l[2] = (row / a.b[1]) % a.b[2];
+    l[3] = row / (a.b[1] * a.b[2]);
+    l[0] = 2 * (i - row * bx2) + ((l[1] + l[2] + l[3] + p) & 1);
+}
+
+__device__ __forceinline__ long long sap_global_cb(const Geom &g, const int G[4])
+{
+    return (G[0] + (long long)g.L[0] * (G[1] + (long long)g.L[1] * (G[2] + (long long)g.L[2] * G[3]))) >> 1;
+}
+
+__device__ __forceinline__ void ld_sm(const float2 *f, int i, cx<float> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        const float2 t = f[c * SAP_THREADS + i];
+        v[c] = {t.x, t.y};
+    }
+}
+
+__device__ __forceinline__ void st_sm(float2 *f, int i, const cx<float> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) f[c * SAP_THREADS + i] = make_float2(v[c].re, v[c].im);
+}
+
+// one direction of the block-local hopping sum at the site with local
+// coordinates l (parity p, global coordinates G): the neighbour is read from
+// the shared-memory field `src` of the other parity when it lies in the block
+template <int MU>
+__device__ __forceinline__ void sap_hop_dir(const SapArgs &a, const float2 *src, const int l[4], const int G[4],
+                                            int p, long long cb, cx<float> acc[12])
+{
+    const int ext = a.b[MU], L = a.g.L[MU];
+    const bool whole = ext == L;   // the block spans the direction: the wrap stays inside
+#pragma unroll
+    for (int dir = 0; dir < 2; dir++) {
+        const int ln = dir == 0 ? l[MU] + 1 : l[MU] - 1;
+        const bool in = whole || (ln >= 0 && ln < ext);
+        if (!in) continue;
+        int q[4] = {l[0], l[1], l[2], l[3]};
+        q[MU] = (ln + ext) % ext;
+        const int nbi = (q[0] + a.b[0] * (q[1] + a.b[1] * (q[2] + a.b[2] * q[3]))) >> 1;
+        cx<float> psi[12];
+        ld_sm(src, nbi, psi);
+        cx<float> m[9];
+        float s = 1.0f;
+        if (dir == 0) {
+            load_link(a.U[p], a.g.stride, MU, cb, m);
+            if (MU == 3 && G[3] + 1 == L) s = (float)a.g.tbc;
+            hop_apply<MU, -1>(acc, psi, m, s);
+        } else {
+            int Gm[4] = {G[0], G[1], G[2], G[3]};
+            Gm[MU] = G[MU] == 0 ? L - 1 : G[MU] - 1;
+            load_link(a.U[1 - p], a.g.stride, MU, sap_global_cb(a.g, Gm), m);
+            if (MU == 3 && G[3] == 0) s = (float)a.g.tbc;
+            hop_apply<MU, +1>(acc, psi, m, s);
+        }
+    }
+}
+
+// acc = sum over the in-block neighbours of (1 -+ g_mu) W psi
+__device__ __forceinline__ void sap_hop(const SapArgs &a, const float2 *src, const int l[4], const int G[4], int p,
+                                        long long cb, cx<float> acc[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = {0.0f, 0.0f};
+    sap_hop_dir<0>(a, src, l, G, p, cb, acc);
+    sap_hop_dir<1>(a, src, l, G, p, cb, acc);
+    sap_hop_dir<2>(a, src, l, G, p, cb, acc);
+    sap_hop_dir<3>(a, src, l, G, p, cb, acc);
+}
+
+// sum over the CTA of three floats (all threads receive the totals)
+__device__ __forceinline__ void sap_sum3(float v[3], float *sh)
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; k++) sh[warp * 3 + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float t = 0.0f;
+        for (int w = 0; w < SAP_THREADS / 32; w++) t += sh[w * 3 + k];
+        v[k] = t;
+    }
+}
+
+// The CTA asks for three resident blocks per SM (at most 168 registers); the
+// MR iterate and residual live in shared memory, not in registers.
+__global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
+{
+    __shared__ float2 smE[12 * SAP_THREADS];   // even: r_hat, then the MR residual, then e_e for the odd update
+    __shared__ float2 smX[12 * SAP_THREADS];   // even: the MR iterate e_e
+    __shared__ float2 smO[12 * SAP_THREADS];   // odd: D_oo^{-1} r_o, then t_o
+    __shared__ float red[3 * (SAP_THREADS / 32)];
+    const int i = threadIdx.x;
+    const bool on = i < a.bvh;
+    const int4 o4 = a.origin[blockIdx.x];
+    const int O[4] = {o4.x, o4.y, o4.z, o4.w};
+    int le[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, Ge[4], Go[4];
+    long long cbe = 0, cbo = 0;
+    if (on) {
+        sap_local(a, i, 0, le);
+        sap_local(a, i, 1, lo);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        Ge[mu] = O[mu] + le[mu];
+        Go[mu] = O[mu] + lo[mu];
+    }
+    if (on) {
+        cbe = sap_global_cb(a.g, Ge);
+        cbo = sap_global_cb(a.g, Go);
+    }
+    const long long st = a.g.stride;
+    cx<float> v[12], w[12];
+
+    // D_oo^{-1} r_o on the odd sites
+    if (on) {
+        load_spinor(a.r[1], st, cbo, v);
+        clover_apply<float>(a.Ci, st, cbo, v, w);
+        st_sm(smO, i, w);
+    }
+    __syncthreads();
+    // r_hat_e = r_e - D_eo D_oo^{-1} r_o = r_e + 1/2 H_eo (D_oo^{-1} r_o); e_e = 0
+    if (on) {
+        load_spinor(a.r[0], st, cbe, v);
+        sap_hop(a, smO, le, Ge, 0, cbe, w);
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
+        st_sm(smE, i, v);
+#pragma unroll
+        for (int k = 0; k < 12; k++) w[k] = {0.0f, 0.0f};
+        st_sm(smX, i, w);
+    }
+    __syncthreads();
+
+    // Minimal Residual on S: p = S res, alpha = (p, res) / (p, p), e += alpha res, res -= alpha p
+    for (int j = 0; j < a.m; j++) {
+        // t_o = D_oo^{-1} (-1/2 H_oe res)
+        if (on) {
+            sap_hop(a, smE, lo, Go, 1, cbo, v);
+#pragma unroll
+            for (int k = 0; k < 12; k++) v[k] = -0.5f * v[k];
+            clover_apply<float>(a.Ci, st, cbo, v, w);
+            st_sm(smO, i, w);
+        }
+        __syncthreads();
+        // p = C res + 1/2 H_eo t_o
+        float d[3] = {0.0f, 0.0f, 0.0f};
+        cx<float> pv[12];
+        if (on) {
+            ld_sm(smE, i, v);
+            clover_apply<float>(a.Ce, st, cbe, v, pv);
+            sap_hop(a, smO, le, Ge, 0, cbe, w);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                pv[k] = pv[k] + 0.5f * w[k];
+                d[0] = fmaf(pv[k].re, v[k].re, fmaf(pv[k].im, v[k].im, d[0]));    // Re (p, res)
+                d[1] = fmaf(pv[k].re, v[k].im, fmaf(-pv[k].im, v[k].re, d[1]));   // Im (p, res)
+                d[2] = fmaf(pv[k].re, pv[k].re, fmaf(pv[k].im, pv[k].im, d[2]));  // (p, p)
+            }
+        }
+        sap_sum3(d, red);
+        const float ar = d[2] > 0.0f ? d[0] / d[2] : 0.0f, ai = d[2] > 0.0f ? d[1] / d[2] : 0.0f;
+        if (on) {
+            ld_sm(smE, i, v);
+            ld_sm(smX, i, w);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                w[k] = w[k] + cx<float>{ar * v[k].re - ai * v[k].im, ar * v[k].im + ai * v[k].re};
+                v[k] = v[k] - cx<float>{ar * pv[k].re - ai * pv[k].im, ar * pv[k].im + ai * pv[k].re};
+            }
+            st_sm(smE, i, v);
+            st_sm(smX, i, w);
+        }
+        __syncthreads();
+    }
+
+    // e_o = D_oo^{-1} (r_o - D_oe e_e) = D_oo^{-1} (r_o + 1/2 H_oe e_e); x += e
+    if (on) {
+        sap_hop(a, smX, lo, Go, 1, cbo, w);
+        load_spinor(a.r[1], st, cbo, v);
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
+        clover_apply<float>(a.Ci, st, cbo, v, w);
+        load_spinor_rw(a.x[1], st, cbo, v);
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = v[k] + w[k];
+        store_spinor(a.x[1], st, cbo, v);
+        ld_sm(smX, i, w);
+        load_spinor_rw(a.x[0], st, cbe, v);
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = v[k] + w[k];
+        store_spinor(a.x[0], st, cbe, v);
+    }
+}
+
+void sap_blocks(const Exec &e, const SapLaunch &s)
+{
+    if (s.count <= 0) return;
+    SapArgs a;
+    a.g = e.g;
+    for (int mu = 0; mu < 4; mu++) a.b[mu] = s.b[mu];
+    a.bvh = s.b[0] * s.b[1] * s.b[2] * s.b[3] / 2;
+    a.origin = s.origin;
+    a.U[0] = (const float4 *)s.U[0];
+    a.U[1] = (const float4 *)s.U[1];
+    a.Ce = (const float4 *)s.Ce;
+    a.Ci = (const float4 *)s.Ci;
+    a.r[0] = (const float4 *)s.r[0];
+    a.r[1] = (const float4 *)s.r[1];
+    a.x[0] = (float4 *)s.x[0];
+    a.x[1] = (float4 *)s.x[1];
+    a.m = s.m;
+    // per block site and parity: the residual in, links and clover once per
+    // hop sweep from L1/L2, x read and written; per MR step two block hops
+    const double sites = (double)s.count * a.bvh;
+    Launch L_(e, K_SAP, sites * (2 * 96 + 2 * 192 + 8 * 48 + 2 * 288),
+              sites * ((2 * s.m + 2) * (1320 + 552) / 1.0 + s.m * 100));
+    sap_block_kernel<<<s.count, SAP_THREADS, 0, e.st>>>(a);
+}
+
+}  // namespace lq

@@ -17,7 +17,7 @@ LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDO
 LQ_F64, LQ_F32, LQ_DF64 = 0, 1, 2
 LQ_OP_FULL, LQ_OP_SCHUR, LQ_OP_SCHUR_DAG, LQ_OP_EE, LQ_OP_OO_INV = range(5)
 LQ_SOLVER_GMRES, LQ_SOLVER_FGMRES = 0, 1
-LQ_SMOOTH_NONE, LQ_SMOOTH_RICHARDSON, LQ_SMOOTH_GMRES = 0, 1, 2
+LQ_SMOOTH_NONE, LQ_SMOOTH_RICHARDSON, LQ_SMOOTH_GMRES, LQ_SMOOTH_SAP = 0, 1, 2, 3
 
 
 class lq_lattice(ctypes.Structure):
@@ -29,7 +29,7 @@ class lq_solver_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("prec", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("smooth_n", ctypes.c_int), ("smooth_m", ctypes.c_int), ("omega", ctypes.c_double),
-                ("smooth_tol", ctypes.c_double), ("inner_prec", ctypes.c_int)]
+                ("smooth_tol", ctypes.c_double), ("inner_prec", ctypes.c_int), ("sap_block", ctypes.c_int * 4)]
 
 
 class lq_stats(ctypes.Structure):
@@ -326,7 +326,7 @@ def lq_counters(ctx):
     return n.value, b.value
 
 
-LQ_K_COUNT = 20
+LQ_K_COUNT = 21
 
 
 def lq_profile(ctx, on: bool) -> None:
@@ -360,6 +360,6 @@ def make_lattice(L, t_bc: int = -1, m0: float = 0.0, csw: float = 1.0) -> lq_lat
 
 def make_params(solver=LQ_SOLVER_GMRES, prec=LQ_F64, tol=1e-10, restart=30, max_restarts=1000,
                 smoother=LQ_SMOOTH_NONE, smooth_n=0, smooth_m=1, omega=0.0, smooth_tol=0.0,
-                inner_prec=LQ_F64) -> lq_solver_params:
+                inner_prec=LQ_F64, sap_block=(0, 0, 0, 0)) -> lq_solver_params:
     return lq_solver_params(solver, prec, tol, restart, max_restarts, smoother, smooth_n, smooth_m,
-                            omega, smooth_tol, inner_prec)
+                            omega, smooth_tol, inner_prec, (ctypes.c_int * 4)(*sap_block))
