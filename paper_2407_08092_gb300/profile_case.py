@@ -6,7 +6,8 @@ GB) and then either applies D_S (K1 + K2) `--apps` times in one precision
 through the C ABI (printing per-class device times), runs `--apps`
 mixed-precision solves (FGMRES(10) in df64 preconditioned by GMRES(16) in
 FP32), a batched solve of `--nrhs` point sources through a one-member group
-(printing the autotuner's choice), or the fermion-force kernel, e.g.
+(printing the autotuner's choice), SAP(3, 4) smoother calls, or the
+fermion-force kernel, e.g.
 ``python -m paper_2407_08092_gb300.profile_case --lattice 24,24,24,48 --prec 1 --apps 3``.
 """
 import argparse
@@ -23,7 +24,7 @@ def main():
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32, 2 df64")
     ap.add_argument("--apps", type=int, default=3)
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force"])
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force", "sap"])
     ap.add_argument("--nrhs", type=int, default=12)
     a = ap.parse_args()
     L = tuple(int(v) for v in a.lattice.split(","))
@@ -62,6 +63,14 @@ def main():
               "ms", round(st[0].time_ms, 2))
         print("tuning (sites/tile, grid, blas blocks, hop pair ms, blas pair ms)", lqdd.lq_group_tuning(grp))
         lqdd.lq_group_destroy(grp)
+    elif a.mode == "sap":
+        r = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()
+        e = torch.empty_like(r)
+        prm = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_SAP, smooth_n=3, smooth_m=4, inner_prec=lqdd.LQ_F32,
+                               prec=lqdd.LQ_DF64)
+        for _ in range(a.apps):
+            lqdd.lq_smooth(ctx, prm, r, e)
+        out = float(e.abs().sum())
     elif a.mode == "force":
         X = torch.from_numpy(synth.gaussian_spinor(V, 71)).cuda()
         Y = torch.from_numpy(synth.gaussian_spinor(V, 72)).cuda()
