@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-sap", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
     return ap.parse_args()
 
 
@@ -367,6 +368,54 @@ def run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks, V, omega):
     return res
 
 
+def run_bf16(lqdd, torch, stream, ctx, db, x, pk, V, omega):
+    """BF16 storage on the benchmark lattice: the D_S apply (1200 algorithmic
+    bytes per site) against FP32 (1824), its relative error against the FP64
+    apply, and FGMRES(10) df64 to 1e-10 preconditioned by Richardson(5) with
+    BF16 against FP32 storage."""
+    Vh = V // 2
+    xe = db[:Vh].contiguous()
+    out = {p: torch.empty_like(xe) for p in (lqdd.LQ_F64, lqdd.LQ_F32, lqdd.LQ_BF16)}
+    res = {}
+    for prec, name in ((lqdd.LQ_F32, "f32"), (lqdd.LQ_BF16, "bf16")):
+        lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, out[prec])
+        lqdd.lq_profile(ctx, 1)
+        for _ in range(20):
+            lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, out[prec])
+        prof = read_profile(lqdd, ctx)
+        lqdd.lq_profile(ctx, 0)
+        k1, k2 = ("hop_k1_f32", "hop_k2_f32") if name == "f32" else ("hop_k1_bf16", "hop_k2_bf16")
+        ms = (prof[k1]["ms"] + prof[k2]["ms"]) / 20
+        by = (prof[k1]["bytes"] + prof[k2]["bytes"]) / 20
+        res[name] = {"ds_us": round(1e3 * ms, 1), "ds_gbs": round(by / (ms / 1e3) / 1e9, 1),
+                     "ds_frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                     "bytes_per_site": round(by / Vh, 1)}
+    lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, lqdd.LQ_F64, xe, out[lqdd.LQ_F64])
+    ref = out[lqdd.LQ_F64]
+    for prec, name in ((lqdd.LQ_F32, "f32"), (lqdd.LQ_BF16, "bf16")):
+        res[name]["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(out[prec] - ref) / torch.linalg.vector_norm(ref))
+    for prec, name in ((lqdd.LQ_F32, "f32"), (lqdd.LQ_BF16, "bf16")):
+        prm = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                               max_restarts=50, smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=omega,
+                               inner_prec=prec)
+        x.zero_()
+        lqdd.lq_solve(ctx, prm, db, x)
+        ts = []
+        for _ in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            status, st = lqdd.lq_solve(ctx, prm, db, x)
+            z.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(z))
+        res[name]["fgmres_richardson5_ms"] = round(sorted(ts)[1], 2)
+        res[name]["fgmres_richardson5_iters"] = st.iters
+        res[name]["fgmres_richardson5_rel_resid_true"] = st.rel_resid_true
+    return res
+
+
 def read_profile(lqdd, ctx):
     """Per-class launches, device ms, algorithmic bytes and flops since lq_profile(ctx, 1)."""
     prof = {}
@@ -530,6 +579,11 @@ def run_ours(args):
     if not args.no_sap:
         sap = run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks=peaks(), V=V, omega=info["omega"])
 
+    # BF16 storage of spinors and links against FP32
+    bf16 = None
+    if not args.no_bf16:
+        bf16 = run_bf16(lqdd, torch, stream, ctx, db, x, peaks(), V, info["omega"])
+
     # batched: 12 spin-colour point sources on each of four lattices
     batched = None
     if not args.no_batch:
@@ -620,6 +674,7 @@ def run_ours(args):
         "batched": batched,
         "force": force,
         "sap": sap,
+        "bf16": bf16,
         "kernels": prof,
         "step_bytes": step_bytes,
     }

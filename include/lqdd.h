@@ -60,12 +60,16 @@ typedef enum {
     LQ_ERR_STATE = 7           /* call out of order (e.g. an operator before lq_set_gauge) */
 } lq_status;
 
+/* LQ_BF16 stores spinors and 12-real links in BF16 (8 significand bits) and
+ * computes in FP32 with the FP32 clover blocks: the low-precision storage of
+ * the mixed-precision scheme.  It is offered for lq_apply (LQ_OP_SCHUR and
+ * LQ_OP_SCHUR_DAG) and as the inner precision of the Richardson smoother. */
 /* Arithmetic precisions.  LQ_DF64 is FP64-accurate "double-float" arithmetic:
  * each real is an unevaluated sum of two floats (about 48 significand bits)
  * combined with the error-free transformations of Knuth and Dekker, so it runs
  * on the FP32 units, which GB300 provides at 64 times its FP64 rate; it meets
  * the same 1e-12 parity bound as LQ_F64 with a float exponent range. */
-typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_DF64 = 2 } lq_prec;
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_DF64 = 2, LQ_BF16 = 3 } lq_prec;
 
 typedef enum {
     LQ_OP_FULL = 0,      /* D on the full lattice: in, out are full spinors */
@@ -291,6 +295,7 @@ typedef enum {
     LQ_K_CLOVER_FIELD,   /* field strengths F_munu of the six planes from the leaves (df64) */
     LQ_K_FORCE,          /* fermion force: clover insertion and per-link gradient (df64) */
     LQ_K_SAP,            /* SAP block solves (FP32) */
+    LQ_K_HOP_K1_BF16, LQ_K_HOP_K2_BF16,   /* K1, K2 (and the fused Richardson form) with BF16 storage */
     LQ_K_COUNT
 } lq_kernel_class;
 

@@ -51,6 +51,7 @@ struct lq_ctx {
     void *Ci64 = nullptr;
     void *Ci32 = nullptr;
     void *Udf[2] = {nullptr, nullptr};
+    void *U16[2] = {nullptr, nullptr};   // BF16 12-real links
     void *Cdf[2] = {nullptr, nullptr};
     void *Cidf = nullptr;
     int *dflag = nullptr;
@@ -130,7 +131,7 @@ void *ws(lq_ctx *c, const std::string &name, size_t bytes)
     return p;
 }
 
-const char *suffix(int prec) { return prec == P64 ? "/64" : prec == P32 ? "/32" : "/df"; }
+const char *suffix(int prec) { return prec == P64 ? "/64" : prec == P32 ? "/32" : prec == P16 ? "/16" : "/df"; }
 
 void *field(lq_ctx *c, int prec, const char *name)
 {
@@ -173,11 +174,15 @@ void need_gauge(lq_ctx *c)
     if (!c->have_gauge) fail(c, LQ_ERR_STATE, "no gauge field: call lq_set_gauge first");
 }
 
+// clover blocks of a precision (BF16 fields use the FP32 blocks)
 const void *Cp(lq_ctx *c, int prec, int parity)
 {
-    return prec == P64 ? c->C64[parity] : prec == P32 ? c->C32[parity] : c->Cdf[parity];
+    return prec == P64 ? c->C64[parity] : (prec == P32 || prec == P16) ? c->C32[parity] : c->Cdf[parity];
 }
-const void *Cip(lq_ctx *c, int prec) { return prec == P64 ? c->Ci64 : prec == P32 ? c->Ci32 : c->Cidf; }
+const void *Cip(lq_ctx *c, int prec)
+{
+    return prec == P64 ? c->Ci64 : (prec == P32 || prec == P16) ? c->Ci32 : c->Cidf;
+}
 bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_DF64; }
 
 HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
@@ -186,7 +191,8 @@ HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
     h.mode = mode;
     h.prec = prec;
     h.pout = pout;
-    for (int p = 0; p < 2; p++) h.U[p] = prec == P64 ? c->U64[p] : prec == P32 ? c->U32[p] : c->Udf[p];
+    for (int p = 0; p < 2; p++)
+        h.U[p] = prec == P64 ? c->U64[p] : prec == P32 ? c->U32[p] : prec == P16 ? c->U16[p] : c->Udf[p];
     return h;
 }
 
@@ -661,7 +667,9 @@ void check_params(lq_ctx *c, const lq_solver_params *p, bool solve)
     if (p->smoother < LQ_SMOOTH_NONE || p->smoother > LQ_SMOOTH_SAP) fail(c, LQ_ERR_ARG, "bad smoother");
     if (p->smoother == LQ_SMOOTH_SAP && (p->inner_prec != LQ_F32 || p->smooth_m < 0))
         fail(c, LQ_ERR_ARG, "SAP runs in LQ_F32 with smooth_m >= 0 Minimal Residual steps");
-    if (!valid_prec(p->inner_prec)) fail(c, LQ_ERR_ARG, "bad inner_prec");
+    if (!valid_prec(p->inner_prec) && p->inner_prec != LQ_BF16) fail(c, LQ_ERR_ARG, "bad inner_prec");
+    if (p->inner_prec == LQ_BF16 && p->smoother != LQ_SMOOTH_RICHARDSON)
+        fail(c, LQ_ERR_ARG, "LQ_BF16 storage is offered for the Richardson smoother");
     if (p->smoother != LQ_SMOOTH_NONE && p->smooth_n < 0) fail(c, LQ_ERR_ARG, "smooth_n < 0");
     if (p->smoother == LQ_SMOOTH_GMRES && (p->smooth_m < 1 || p->smooth_m > MAX_RESTART))
         fail(c, LQ_ERR_ARG, "smooth_m out of range 1..256");
@@ -1252,11 +1260,13 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
                 c->Cdf[p] = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
             }
             c->Cidf = dev_alloc(c, (size_t)2 * 18 * g.stride * 16);
+            for (int p = 0; p < 2; p++) c->U16[p] = dev_alloc(c, (size_t)4 * 3 * g.stride * 8);
         }
         c->have_gauge = false;
         // links in all three precisions; clover and inverse built in df64 and
         // rounded to the FP64 and FP32 copies
         import_links(e, U, c->U64, c->U32, c->Udf);
+        for (int p = 0; p < 2; p++) links_to_bf16(e, c->U32[p], c->U16[p]);
         const void *udf[2] = {c->Udf[0], c->Udf[1]};
         clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
@@ -1277,7 +1287,9 @@ lq_status lq_apply(lq_ctx *c, int op, int prec, const void *in, void *out)
 {
     return guarded(c, [&] {
         if (!in || !out) fail(c, LQ_ERR_ARG, "NULL field");
-        if (!valid_prec(prec)) fail(c, LQ_ERR_ARG, "bad precision");
+        if (!valid_prec(prec) && prec != LQ_BF16) fail(c, LQ_ERR_ARG, "bad precision");
+        if (prec == LQ_BF16 && op != LQ_OP_SCHUR && op != LQ_OP_SCHUR_DAG)
+            fail(c, LQ_ERR_ARG, "LQ_BF16 applies LQ_OP_SCHUR and LQ_OP_SCHUR_DAG");
         need_gauge(c);
         Exec e = c->ex();
         void *a = field(c, prec, "apply:a"), *b = field(c, prec, "apply:b");
@@ -1905,7 +1917,8 @@ const char *lq_kernel_class_name(int cls)
     static const char *names[K_COUNT] = {"hop_k1_f64", "hop_k1_f32", "hop_k2_f64", "hop_k2_f32", "hop_other",
                                          "clover", "layout", "dot_f64", "dot_f32", "axpy_f64", "axpy_f32",
                                          "norm", "reduce_finish", "copy", "hop_k1_df64", "hop_k2_df64",
-                                         "dot_df64", "axpy_df64", "clover_field", "force", "sap"};
+                                         "dot_df64", "axpy_df64", "clover_field", "force", "sap",
+                                         "hop_k1_bf16", "hop_k2_bf16"};
     return (cls >= 0 && cls < K_COUNT) ? names[cls] : "";
 }
 

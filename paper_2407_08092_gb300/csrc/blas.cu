@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(RT) axpby_df_kernel(df64 ar, df64 ai, const df
 
 // ---- launchers -------------------------------------------------------------------------
 static inline unsigned nblk(long long n) { return (unsigned)((n + RT - 1) / RT); }
-static inline double sp_bytes(int prec) { return prec == P32 ? 96.0 : 192.0; }
+static inline double sp_bytes(int prec) { return prec == P32 ? 96.0 : prec == P16 ? 48.0 : 192.0; }
 static inline long long nvec(const Geom &g, int prec) { return (prec == P32 ? 6 : 12) * g.stride; }
 static inline int axpy_class(int prec) { return prec == P64 ? K_AXPY_F64 : prec == P32 ? K_AXPY_F32 : K_AXPY_DF; }
 static inline int dot_class(int prec) { return prec == P64 ? K_DOT_F64 : prec == P32 ? K_DOT_F32 : K_DOT_DF; }
@@ -335,6 +335,10 @@ void copy(const Exec &e, int prec, const void *x, void *y)
 
 void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi, void *y, int nfields)
 {
+    if (prec == P16) {
+        bf16_axpby(e, ar, ai, x, br, bi, y, nfields);
+        return;
+    }
     // nfields consecutive fields are one linear array
     Launch L_(e, axpy_class(prec), 3.0 * nfields * e.g.Vh * sp_bytes(prec), (double)nfields * e.g.Vh * 12 * 14);
     const long long n = nvec(e.g, prec) * nfields;

@@ -13,6 +13,7 @@
 // The spin projection and transport of one hop live in spin.cuh.
 #include <type_traits>
 
+#include "bf16.cuh"
 #include "lq_kernels.h"
 #include "spin.cuh"
 
@@ -32,8 +33,8 @@ static_assert(LQ_HOP_THREADS == kHopBlock, "hopping block size");
 
 // one hop: acc += (1 -+ g_mu) W psi(nb), W = U_mu(x) (SIGN -1) or U_mu(x-mu)^+ (SIGN +1);
 // `bsign` is the fermion boundary factor of this hop
-template <int MU, int SIGN, typename R, typename V>
-__device__ __forceinline__ void hop_dir(cx<R> acc[12], const V *__restrict__ psi, const V *__restrict__ U,
+template <int MU, int SIGN, typename R, typename SV, typename LV>
+__device__ __forceinline__ void hop_dir(cx<R> acc[12], const SV *__restrict__ psi, const LV *__restrict__ U,
                                         long long link_site, long long nb, long long stride, R bsign)
 {
     cx<R> p[12];
@@ -60,11 +61,11 @@ struct HopArgs {
 };
 
 
-template <typename R, int MODE>
-__device__ __forceinline__ void hop_body(const Geom &g, const typename St<R>::vec *Uout,
-                                         const typename St<R>::vec *Uin, const typename St<R>::vec *clov, R omega,
-                                         const typename St<R>::vec *in, const typename St<R>::vec *in2,
-                                         const typename St<R>::vec *bv, typename St<R>::vec *out, long long s,
+// SV, LV, CV: storage vectors of the spinors, links and clover blocks (the same
+// type for FP64, FP32 and df64; BF16 spinors and links with FP32 clover)
+template <typename R, int MODE, typename SV, typename LV, typename CV>
+__device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV *Uin, const CV *clov, R omega,
+                                         const SV *in, const SV *in2, const SV *bv, SV *out, long long s,
                                          const Coords &c)
 {
     const long long st = g.stride;
@@ -183,6 +184,40 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel_multi(Geom g, HopAr
                       k.b ? k.b + o : nullptr, k.out + o, s, c);
 }
 
+// BF16 spinors and links, FP32 clover and arithmetic (all modes)
+struct HopArgsBF {
+    const BfS4 *in, *in2, *b;
+    BfS4 *out;
+    const BfL2 *Uout, *Uin;
+    const float4 *clov;
+    float omega;
+    int pout;
+};
+template <int MODE>
+__global__ void LQ_HOP_BOUNDS hop_kernel_bf(Geom g, HopArgsBF k)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.Vh) return;
+    const Coords c = cb_coords(g, s, k.pout);
+    hop_body<float, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+}
+
+template <int MODE>
+static void launch_hop_bf(const Exec &e, const HopCall &c)
+{
+    HopArgsBF k;
+    k.in = (const BfS4 *)c.in;
+    k.in2 = (const BfS4 *)c.in2;
+    k.b = (const BfS4 *)c.b;
+    k.out = (BfS4 *)c.out;
+    k.Uout = (const BfL2 *)c.U[c.pout];
+    k.Uin = (const BfL2 *)c.U[1 - c.pout];
+    k.clov = (const float4 *)c.clov;
+    k.omega = (float)c.omega;
+    k.pout = c.pout;
+    hop_kernel_bf<MODE><<<(unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS), LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+}
+
 // The batched hop over the right-hand sides of several lattices of different
 // sizes in one persistent launch: each block walks the work table, an entry
 // naming a lattice, a block of blockDim.x consecutive sites and the first of
@@ -209,7 +244,7 @@ __global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
         const Coords c = cb_coords(g, s, pout);
         const long long o = L->off + r * L->fs;
         hop_body<float, MODE>(g, L->U[pout], L->U[1 - pout], L->clov[pout], 0.0f, in + o,
-                              in2 ? in2 + o : nullptr, nullptr, out + o, s, c);
+                              in2 ? in2 + o : nullptr, (const float4 *)nullptr, out + o, s, c);
     }
 }
 
@@ -422,10 +457,10 @@ static void launch_hop(const Exec &e, const HopCall &c)
 // the 8-byte-per-real layout)
 static double hop_site_bytes(int mode, int prec, int nrhs)
 {
-    const bool wide = prec != P32;
-    const double sp = wide ? 192.0 : 96.0;          // spinor
-    const double lk = wide ? 144.0 : 48.0;          // link (18 / 12 reals)
-    const double cl = wide ? 576.0 : 288.0;         // 72-real clover pair
+    const bool wide = prec == P64 || prec == PDF;
+    const double sp = wide ? 192.0 : prec == P16 ? 48.0 : 96.0;   // spinor
+    const double lk = wide ? 144.0 : prec == P16 ? 24.0 : 48.0;   // link (18 / 12 reals)
+    const double cl = wide ? 576.0 : 288.0;                       // 72-real clover pair (FP32 for BF16)
     double once = 8 * lk, per = sp + sp;            // links; neighbours and output per rhs
     switch (mode) {
     case HOP_K1: once += cl; break;
@@ -439,6 +474,7 @@ static double hop_site_bytes(int mode, int prec, int nrhs)
 
 static int hop_class(int mode, int prec)
 {
+    if (prec == P16) return mode == HOP_K1 ? K_HOP_K1_BF16 : (mode == HOP_K2 || mode == HOP_RICH) ? K_HOP_K2_BF16 : K_HOP_OTHER;
     if (mode == HOP_K1) return prec == P64 ? K_HOP_K1_F64 : prec == P32 ? K_HOP_K1_F32 : K_HOP_K1_DF;
     if (mode == HOP_K2 || mode == HOP_RICH) return prec == P64 ? K_HOP_K2_F64 : prec == P32 ? K_HOP_K2_F32 : K_HOP_K2_DF;
     return K_HOP_OTHER;
@@ -481,6 +517,7 @@ void hop(const Exec &e, const HopCall &c)
     case M:                                                                     \
         if (c.prec == P64) launch_hop<double, M>(e, c);                         \
         else if (c.prec == P32) launch_hop<float, M>(e, c);                     \
+        else if (c.prec == P16) launch_hop_bf<M>(e, c);                         \
         else launch_hop<df64, M>(e, c);                                         \
         break;
     Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec, c.nrhs),

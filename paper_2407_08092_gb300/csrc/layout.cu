@@ -191,6 +191,10 @@ __global__ void export_full_df_kernel(Geom g, const df2 *__restrict__ fe, const 
 
 void import_half(const Exec &e, int prec, const void *nat, void *f)
 {
+    if (prec == P16) {
+        bf16_import_half(e, nat, f);
+        return;
+    }
     Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P32 ? 96 : 192)));
     if (prec == PDF) {
         import_half_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (df2 *)f);
@@ -204,6 +208,10 @@ void import_half(const Exec &e, int prec, const void *nat, void *f)
 
 void export_half(const Exec &e, int prec, const void *f, void *nat)
 {
+    if (prec == P16) {
+        bf16_export_half(e, f, nat);
+        return;
+    }
     Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P32 ? 96 : 192)));
     if (prec == PDF) {
         export_half_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const df2 *)f, (double2 *)nat);
@@ -308,6 +316,10 @@ __global__ void df2f_kernel(Geom g, const df2 *__restrict__ in, float4 *out)
 
 void convert(const Exec &e, int from, const void *in, int to, void *out)
 {
+    if (from == P16 || to == P16) {
+        bf16_convert(e, from, in, to, out);
+        return;
+    }
     if (from == to) {
         copy(e, from, in, out);
         return;
@@ -362,6 +374,10 @@ __global__ void gamma5_df_kernel(Geom g, const float4 *in, float4 *out)
 
 void gamma5(const Exec &e, int prec, const void *in, void *out)
 {
+    if (prec == P16) {
+        bf16_gamma5(e, in, out);
+        return;
+    }
     Launch L_(e, K_LAYOUT, (double)e.g.Vh * 2 * (prec == P32 ? 96 : 192));
     if (prec == PDF) {
         gamma5_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)in, (float4 *)out);

@@ -9,16 +9,18 @@
 
 namespace lq {
 
-// Internal precisions: native FP64, FP32, and double-float (df64: FP64-accurate
-// arithmetic on the FP32 units, stored as float pairs in the FP64 layouts).
-enum Prec { P64 = 0, P32 = 1, PDF = 2 };
+// Internal precisions: native FP64, FP32, double-float (df64: FP64-accurate
+// arithmetic on the FP32 units, stored as float pairs in the FP64 layouts), and
+// BF16 storage of spinors and links with FP32 arithmetic and FP32 clover.
+enum Prec { P64 = 0, P32 = 1, PDF = 2, P16 = 3 };
 
 // Kernel classes for the per-class device timing (mirrors lq_kernel_class of
 // the public header).
 enum KClass {
     K_HOP_K1_F64 = 0, K_HOP_K1_F32, K_HOP_K2_F64, K_HOP_K2_F32, K_HOP_OTHER, K_CLOVER, K_LAYOUT,
     K_DOT_F64, K_DOT_F32, K_AXPY_F64, K_AXPY_F32, K_NORM, K_FINISH, K_COPY,
-    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_FORCE, K_SAP, K_COUNT
+    K_HOP_K1_DF, K_HOP_K2_DF, K_DOT_DF, K_AXPY_DF, K_CLOVER_FIELD, K_FORCE, K_SAP, K_HOP_K1_BF16,
+    K_HOP_K2_BF16, K_COUNT
 };
 
 // Optional CUDA-event timing of every launch (enabled by lq_profile).
@@ -76,12 +78,21 @@ struct Launch {
 // Bytes of one internal per-parity spinor field in a precision.
 inline size_t spinor_bytes(const Geom &g, int prec)
 {
-    return (size_t)24 * g.stride * (prec == P32 ? 4 : 8);
+    return (size_t)24 * g.stride * (prec == P32 ? 4 : prec == P16 ? 2 : 8);
 }
 
 // ---- layout (layout.cu) ----------------------------------------------------
 // natural complex-double gauge field -> per-parity internal link copies
 void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2], void *Udf[2]);
+// BF16 12-real links of one parity from the FP32 ones
+void links_to_bf16(const Exec &e, const void *U32, void *U16);
+// BF16 fields (bf16.cu): conversions (one side BF16), natural half spinors,
+// gamma5 and axpby; the generic launchers below dispatch here for P16
+void bf16_convert(const Exec &e, int from, const void *in, int to, void *out);
+void bf16_import_half(const Exec &e, const void *nat, void *f);
+void bf16_export_half(const Exec &e, const void *f, void *nat);
+void bf16_gamma5(const Exec &e, const void *in, void *out);
+void bf16_axpby(const Exec &e, double ar, double ai, const void *x, double br, double bi, void *y, int nfields);
 // natural half spinor [Vh][12] c128 <-> internal field of one parity
 void import_half(const Exec &e, int prec, const void *nat, void *f);
 void export_half(const Exec &e, int prec, const void *f, void *nat);

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblqdd.so")
 
 LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN, LQ_ERR_NAN, LQ_ERR_STATE = range(8)
-LQ_F64, LQ_F32, LQ_DF64 = 0, 1, 2
+LQ_F64, LQ_F32, LQ_DF64, LQ_BF16 = 0, 1, 2, 3
 LQ_OP_FULL, LQ_OP_SCHUR, LQ_OP_SCHUR_DAG, LQ_OP_EE, LQ_OP_OO_INV = range(5)
 LQ_SOLVER_GMRES, LQ_SOLVER_FGMRES = 0, 1
 LQ_SMOOTH_NONE, LQ_SMOOTH_RICHARDSON, LQ_SMOOTH_GMRES, LQ_SMOOTH_SAP = 0, 1, 2, 3
@@ -326,7 +326,7 @@ def lq_counters(ctx):
     return n.value, b.value
 
 
-LQ_K_COUNT = 21
+LQ_K_COUNT = 23
 
 
 def lq_profile(ctx, on: bool) -> None:
