@@ -473,6 +473,17 @@ def run_force(lqdd, synth, torch, stream, dev, pk):
         lqdd.lq_destroy(ctx)
 
 
+def combine_ranks(dist, torch, device, ms, tot_bytes, e2e_ms):
+    """Replicas: the timed region of the whole job is the slowest rank's (max
+    over ranks), the work is every rank's (bytes summed over ranks)."""
+    t = torch.tensor([ms, tot_bytes, e2e_ms], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1]), float(tmax[2])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -618,14 +629,9 @@ def run_ours(args):
     # max over ranks of the timed region, bytes summed over ranks
     tot_bytes = step_bytes * args.steps
     if dist:
-        t = torch.tensor([ms, tot_bytes, (e2e or {}).get("ms_per_step", 0.0)], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, tot_bytes = float(tmax[0]), float(tsum[1])
+        ms, tot_bytes, e2e_ms = combine_ranks(dist, torch, dev, ms, tot_bytes, (e2e or {}).get("ms_per_step", 0.0))
         if e2e:
-            e2e["ms_per_step"] = float(tmax[2])
+            e2e["ms_per_step"] = e2e_ms
     lqdd.lq_destroy(ctx)
     if rank != 0:
         if dist:
