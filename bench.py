@@ -10,7 +10,7 @@ a_k ~ N(0,1) (seed 1001), c_sw = 1.0, m0 = 0.02, Gaussian complex source
   2. lq_estimate_norm  10 FP32 power iterations on D_S^+ D_S -> omega     (a8)
   3. lq_smooth         odd-even Richardson(5, delta = 0.8) smoother M_5 r (a6, a7)
   4. lq_solve          odd-even FGMRES(10) in df64 (FP64-accurate double-float),
-                       right-preconditioned by GMRES(16) in FP32 to 1e-5, to a
+                       right-preconditioned by GMRES(8) in FP32 to 1e-5, to a
                        1e-10 residual                                      (a4-a6, a9-a11)
 
 value = algorithmic bytes of every library kernel in the timed steps (the
@@ -249,7 +249,7 @@ def run_batched(lqdd, synth, torch, stream, dev):
     """The batched workload: 12 spin-colour point sources (at the origin) on each
     of 24^3 x 48, 8^4, 16^4 and 16^3 x 32, each lattice with its own links (eps
     0.25, m0 0.05, c_sw 1), all solved to 1e-10 by one lq_solve_group (df64
-    defect correction around one batched FP32 GMRES(16) whose operator launches
+    defect correction around one batched FP32 GMRES(8) whose operator launches
     are single persistent grids over every lattice and right-hand side, cycles
     replayed from CUDA graphs, launch shapes autotuned), against one
     lq_solve_batch per lattice, 48 single mixed solves, and 48 plain FP64
@@ -269,9 +269,9 @@ def run_batched(lqdd, synth, torch, stream, dev):
             bs.append(b)
             xs.append(torch.zeros_like(b))
         grp = lqdd.lq_group_create(ctxs, stream.cuda_stream)
-        bp = lqdd.make_batch_params(tol=1e-10, restart=16, max_restarts=10, smooth_n=8, smooth_tol=1e-5)
+        bp = lqdd.make_batch_params(tol=1e-10, restart=8, max_restarts=10, smooth_n=16, smooth_tol=1e-5)
         single = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                                  max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                                  max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
                                   smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
         fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
 
@@ -317,7 +317,7 @@ def run_batched(lqdd, synth, torch, stream, dev):
         res["speedup_vs_fp64"] = round(res["fp64_sequential"]["ms"] / res["group"]["ms"], 2)
         res["config"] = ("12 spin-colour point sources on each of 24^3x48, 8^4, 16^4, 16^3x32 (own links, eps 0.25, "
                          "m0 0.05, csw 1), 48 systems, all to 1e-10; group: one lq_solve_group; per_lattice: "
-                         "lq_solve_batch per lattice; sequential: 48 x FGMRES(10) df64 / GMRES(16) FP32; "
+                         "lq_solve_batch per lattice; sequential: 48 x FGMRES(10) df64 / GMRES(8) FP32; "
                          "fp64_sequential: 48 x plain FP64 GMRES(30); medians")
         lqdd.lq_group_destroy(grp)
         return res
@@ -440,7 +440,7 @@ def run_force(lqdd, synth, torch, stream, dev, pk):
         phi = torch.from_numpy(synth.gaussian_spinor(V, 2004)).to(dev)
         G = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device=dev)
         prm = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                               max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                               max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
                                smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
         X, Y = torch.empty_like(phi), torch.empty_like(phi)
         lqdd.lq_fermion_force(ctx, prm, phi, G)                      # workspace
@@ -516,7 +516,7 @@ def run_ours(args):
     x = torch.zeros_like(db)
     e = torch.empty_like(db)
     mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
                              smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
     info = {}
 
@@ -658,7 +658,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": "32^3x64 odd-even Wilson-clover step: set_gauge + 10 FP32 power iterations + "
-                               "Richardson(5) FP32 smoother + FGMRES(10) df64 / GMRES(16) FP32 solve to 1e-10",
+                               "Richardson(5) FP32 smoother + FGMRES(10) df64 / GMRES(8) FP32 solve to 1e-10",
                    "lattice": list(L_WORK), "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC,
                    "l2": "inputs larger than L2 (gauge field 1.2 GB, each spinor field 0.4 GB); no flush",
                    "parallelism": "replicas" if world > 1 else "single"},

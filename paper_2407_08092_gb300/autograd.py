@@ -30,7 +30,7 @@ class FermionAction:
         self.ctx = lqdd.lq_create(lqdd.make_lattice(self.L, t_bc, m0, csw), s.cuda_stream)
         self.params = params if params is not None else lqdd.make_params(
             solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-12, restart=10, max_restarts=50,
-            smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16, smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+            smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8, smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
         self._key = None
         self._ref = None
         self.last_stats = None

@@ -308,7 +308,7 @@ def lq_group_tuning(grp):
     return a.value, b.value, c.value, d.value, e.value
 
 
-def make_batch_params(tol=1e-10, restart=16, max_restarts=10, smooth_n=8, smooth_tol=1e-5) -> lq_solver_params:
+def make_batch_params(tol=1e-10, restart=8, max_restarts=10, smooth_n=16, smooth_tol=1e-5) -> lq_solver_params:
     """Parameters of lq_solve_batch: df64 defect correction around batched FP32 GMRES(restart)."""
     return make_params(solver=LQ_SOLVER_GMRES, prec=LQ_DF64, tol=tol, restart=restart, max_restarts=max_restarts,
                        smoother=LQ_SMOOTH_GMRES, smooth_n=smooth_n, smooth_m=restart, smooth_tol=smooth_tol,

@@ -4,7 +4,7 @@ Builds a context on a seeded lattice (default 24^3 x 48, whose per-launch
 working set is larger than L2 but whose device footprint stays within a few
 GB) and then either applies D_S (K1 + K2) `--apps` times in one precision
 through the C ABI (printing per-class device times), runs `--apps`
-mixed-precision solves (FGMRES(10) in df64 preconditioned by GMRES(16) in
+mixed-precision solves (FGMRES(10) in df64 preconditioned by GMRES(8) in
 FP32), a batched solve of `--nrhs` point sources through a one-member group
 (printing the autotuner's choice), SAP(3, 4) smoother calls, or the
 fermion-force kernel, e.g.
@@ -87,7 +87,7 @@ def main():
         b = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()
         x = torch.zeros_like(b)
         p = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=20, smooth_m=16,
+                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
                              smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
         for _ in range(a.apps):
             x.zero_()
