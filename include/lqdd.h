@@ -235,12 +235,20 @@ lq_status lq_solve_group(lq_group *grp, const lq_solver_params *params, const in
  * current layout and captured graphs. */
 lq_status lq_group_set_autotune(lq_group *grp, int on);
 
-/* The launch shapes in use after a solve: sites per tile of the batched hop
- * (right-hand sides per tile = 128 / sites), its grid, BLAS blocks per system,
+/* Pin the launch shape of the batched hop instead of autotuning it:
+ * sites_per_tile 16, 32, 64 or 128, rhs_per_thread 1 or 2, grid_factor 1 or 2
+ * (times the resident blocks, persistent) or 0 (one block per tile).  The BLAS
+ * blocking keeps its default.  Drops the current layout and captured graphs;
+ * lq_group_set_autotune(grp, 1) returns to autotuning. */
+lq_status lq_group_set_shape(lq_group *grp, int sites_per_tile, int rhs_per_thread, int grid_factor);
+
+/* The launch shapes in use after a solve: sites per tile of the batched hop,
+ * right-hand sides per thread (1 or 2; right-hand sides per tile =
+ * rhs_per_thread * 128 / sites_per_tile), its grid, BLAS blocks per system,
  * and the measured times of the chosen hop pair and BLAS pair (0 if untuned).
  * LQ_ERR_STATE before the first solve.  Any pointer may be NULL. */
-lq_status lq_group_tuning(lq_group *grp, int *sites_per_tile, int *grid, int *blas_blocks, double *hop_ms,
-                          double *blas_ms);
+lq_status lq_group_tuning(lq_group *grp, int *sites_per_tile, int *rhs_per_thread, int *grid, int *blas_blocks,
+                          double *hop_ms, double *blas_ms);
 
 /* Gradient of the bilinear form b(U) = Re(Y^+ D(U) X) with respect to every
  * link, for given full spinors X and Y (no paper counterpart: the operator is

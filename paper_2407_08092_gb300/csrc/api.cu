@@ -714,6 +714,7 @@ struct lq_group {
     cudaStream_t st = nullptr;     // private stream (graph capture)
     cudaEvent_t ev = nullptr;
     bool autotune = true;
+    int pin_spt = 32, pin_rpt = 1, pin_factor = 2;   // the shape used without autotuning
     // layout of the current signature: right-hand sides per member, cycle length
     std::vector<int> nrhs;
     int N = 0, m = 0;
@@ -726,7 +727,7 @@ struct lq_group {
     int ntiles = 0, max_tiles = 0, blas_default = 1, blas_max = 1;
     double k1_bytes = 0, k2_bytes = 0, k1_flops = 0, k2_flops = 0;
     struct {
-        int spt = 32, grid = 0, blas = 0;
+        int spt = 32, rpt = 1, grid = 0, blas = 0;
         float hop_ms = 0.0f, blas_ms = 0.0f;
         bool tuned = false;
     } tune;
@@ -786,9 +787,9 @@ void group_release(lq_group *G)
 // the work table of the batched hop for `spt` sites per tile: per member, per
 // site block, its right-hand-side groups (so the tiles of one site block follow
 // one another)
-void group_tiles(lq_group *G, int spt)
+void group_tiles(lq_group *G, int spt, int per_thread = 1)
 {
-    const int rpt = kHopBlock / spt;
+    const int rpt = per_thread * (kHopBlock / spt);   // right-hand sides per tile
     std::vector<int4> t;
     for (size_t l = 0; l < G->mem.size(); l++) {
         const long long sb = (G->mem[l]->g.Vh + spt - 1) / spt;
@@ -803,6 +804,7 @@ void group_tiles(lq_group *G, int spt)
     ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
     G->ntiles = (int)t.size();
     G->tune.spt = spt;
+    G->tune.rpt = per_thread;
 }
 
 // persistent grid: `factor` times the resident blocks of the whole GPU (0: one
@@ -812,7 +814,7 @@ int group_grid(lq_group *G, int factor)
     if (factor == 0) return G->ntiles;
     int sms = 0;
     ck(gctx(G), cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gctx(G)->device), "cudaDeviceGetAttribute");
-    const long long g = (long long)factor * hop_group_resident() * sms;
+    const long long g = (long long)factor * hop_group_resident(G->tune.rpt) * sms;
     return (int)(g < G->ntiles ? g : G->ntiles);
 }
 
@@ -912,8 +914,8 @@ void group_setup(lq_group *G, const std::vector<int> &nrhs, int m)
     ck(c, cudaMallocHost((void **)&G->h, sizeof(double) * 3 * N), "cudaMallocHost");
     ck(c, cudaMallocHost((void **)&G->hact, sizeof(int) * N), "cudaMallocHost");
     G->nrhs = nrhs;
-    group_tiles(G, 32);
-    G->tune.grid = group_grid(G, 2);
+    group_tiles(G, G->pin_spt, G->pin_rpt);
+    G->tune.grid = group_grid(G, G->pin_factor);
     G->tune.blas = G->blas_default;
     G->tune.tuned = false;
 }
@@ -922,10 +924,10 @@ void group_setup(lq_group *G, const std::vector<int> &nrhs, int m)
 void group_schur(lq_group *G, const void *in, void *out)
 {
     Exec e = gexec(G);
-    hop_group(e, HOP_K1, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, in, nullptr, G->T, G->k1_bytes,
-              G->k1_flops);
-    hop_group(e, HOP_K2, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, G->T, in, out, G->k2_bytes,
-              G->k2_flops);
+    hop_group(e, HOP_K1, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, G->tune.rpt, in, nullptr, G->T,
+              G->k1_bytes, G->k1_flops);
+    hop_group(e, HOP_K2, G->desc, G->tiles, G->ntiles, G->tune.grid, G->tune.spt, G->tune.rpt, G->T, in, out,
+              G->k2_bytes, G->k2_flops);
 }
 
 void group_set_blas(lq_group *G, int blocks)
@@ -937,9 +939,9 @@ void group_set_blas(lq_group *G, int blocks)
 
 // The autotuner: times every candidate launch shape on the group's own buffers
 // (CUDA events, after a warm-up launch) and keeps the fastest.
-//   batched hop: sites per tile 16, 32, 64, 128 (with 8, 4, 2, 1 right-hand
-//     sides per tile) x grid = 1 or 2 times the resident blocks (persistent) or
-//     one block per tile;
+//   batched hop: one or two right-hand sides per thread x sites per tile 16,
+//     32, 64, 128 (with 8, 4, 2, 1 threads along the right-hand sides) x grid =
+//     1 or 2 times the resident blocks (persistent) or one block per tile;
 //   batched BLAS: blocks per system 1/2, 1, 2 times the default, on a
 //     multi-dot and a multi-axpy over min(m, 8) basis vectors.
 // Launch counts and bytes of the trials are not recorded.
@@ -963,20 +965,22 @@ void group_tune(lq_group *G)
         return ms / 3.0f;
     };
     float best = 1e30f;
-    int best_spt = 32, best_factor = 2;
-    for (int spt : {32, 64, 16, 128}) {
-        group_tiles(G, spt);
-        for (int factor : {1, 2, 0}) {
-            G->tune.grid = group_grid(G, factor);
-            const float t = timed([&] { group_schur(G, G->X, G->V); });
-            if (t < best) {
-                best = t;
-                best_spt = spt;
-                best_factor = factor;
+    int best_spt = 32, best_rpt = 1, best_factor = 2;
+    for (int rpt : {1, 2})
+        for (int spt : {32, 64, 16, 128}) {
+            group_tiles(G, spt, rpt);
+            for (int factor : {1, 2, 0}) {
+                G->tune.grid = group_grid(G, factor);
+                const float t = timed([&] { group_schur(G, G->X, G->V); });
+                if (t < best) {
+                    best = t;
+                    best_spt = spt;
+                    best_rpt = rpt;
+                    best_factor = factor;
+                }
             }
         }
-    }
-    group_tiles(G, best_spt);
+    group_tiles(G, best_spt, best_rpt);
     G->tune.grid = group_grid(G, best_factor);
     G->tune.hop_ms = best;
     const int nv = G->m < 8 ? G->m : 8;
@@ -1543,12 +1547,33 @@ lq_status lq_group_set_autotune(lq_group *G, int on)
     if (!G) return LQ_ERR_ARG;
     return guarded(gctx(G), [&] {
         G->autotune = on != 0;
+        if (!G->autotune) {   // the fixed default shape
+            G->pin_spt = 32;
+            G->pin_rpt = 1;
+            G->pin_factor = 2;
+        }
         group_release(G);   // the next solve lays out, tunes (or not) and captures afresh
     });
 }
 
-lq_status lq_group_tuning(lq_group *G, int *sites_per_tile, int *grid, int *blas_blocks, double *hop_ms,
-                          double *blas_ms)
+lq_status lq_group_set_shape(lq_group *G, int sites_per_tile, int rhs_per_thread, int grid_factor)
+{
+    if (!G) return LQ_ERR_ARG;
+    return guarded(gctx(G), [&] {
+        const int spt = sites_per_tile;
+        if ((spt != 16 && spt != 32 && spt != 64 && spt != 128) || (rhs_per_thread != 1 && rhs_per_thread != 2) ||
+            grid_factor < 0 || grid_factor > 2)
+            fail(gctx(G), LQ_ERR_ARG, "bad launch shape");
+        G->autotune = false;
+        G->pin_spt = spt;
+        G->pin_rpt = rhs_per_thread;
+        G->pin_factor = grid_factor;
+        group_release(G);
+    });
+}
+
+lq_status lq_group_tuning(lq_group *G, int *sites_per_tile, int *rhs_per_thread, int *grid, int *blas_blocks,
+                          double *hop_ms, double *blas_ms)
 {
     if (!G) return LQ_ERR_ARG;
     if (!G->N) {
@@ -1556,6 +1581,7 @@ lq_status lq_group_tuning(lq_group *G, int *sites_per_tile, int *grid, int *blas
         return LQ_ERR_STATE;
     }
     if (sites_per_tile) *sites_per_tile = G->tune.spt;
+    if (rhs_per_thread) *rhs_per_thread = G->tune.rpt;
     if (grid) *grid = G->tune.grid;
     if (blas_blocks) *blas_blocks = G->tune.blas;
     if (hop_ms) *hop_ms = G->tune.tuned ? G->tune.hop_ms : 0.0;

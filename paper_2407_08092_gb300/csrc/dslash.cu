@@ -145,6 +145,91 @@ __device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV
 // right-hand sides, so each site's links and clover block come from DRAM once
 // and from the caches for the other right-hand sides; it is a separate
 // instantiation so that the single right-hand-side kernel keeps its registers.
+// Two right-hand sides per thread (K1 and K2 of the batched hop): each link is
+// loaded once and transports both neighbour spinors.
+template <int MU, int SIGN>
+__device__ __forceinline__ void hop_dir2(cx<float> acc0[12], cx<float> acc1[12], const float4 *__restrict__ psi0,
+                                         const float4 *__restrict__ psi1, const float4 *__restrict__ U,
+                                         long long link_site, long long nb, long long stride, float bsign)
+{
+    cx<float> m[9];
+    load_link(U, stride, MU, link_site, m);
+    cx<float> p[12];
+    load_spinor(psi0, stride, nb, p);
+    hop_apply<MU, SIGN>(acc0, p, m, bsign);
+    load_spinor(psi1, stride, nb, p);
+    hop_apply<MU, SIGN>(acc1, p, m, bsign);
+}
+
+template <int MODE>
+__device__ __forceinline__ void hop_body2(const Geom &g, const float4 *Uout, const float4 *Uin, const float4 *clov,
+                                          const float4 *in0, const float4 *in1, const float4 *in20,
+                                          const float4 *in21, float4 *out0, float4 *out1, bool two, long long s,
+                                          const Coords &c)
+{
+    const long long st = g.stride;
+    cx<float> a0[12], a1[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) a0[i] = a1[i] = {0.0f, 0.0f};
+    {
+        const long long base = c.row * g.Lxh;
+        const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
+        const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
+        const long long nf = base + (xp >> 1), nb = base + (xm >> 1);
+        hop_dir2<0, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
+        hop_dir2<0, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
+    }
+    {
+        const long long d = g.Lxh;
+        const long long nf = (c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d;
+        const long long nb = (c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d;
+        hop_dir2<1, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
+        hop_dir2<1, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
+    }
+    {
+        const long long d = (long long)g.Lxh * g.L[1];
+        const long long nf = (c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d;
+        const long long nb = (c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d;
+        hop_dir2<2, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
+        hop_dir2<2, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
+    }
+    {
+        const long long d = (long long)g.Lxh * g.L[1] * g.L[2];
+        const bool last = (c.t + 1 == g.L[3]), first = (c.t == 0);
+        const long long nf = last ? s - (long long)(g.L[3] - 1) * d : s + d;
+        const long long nb = first ? s + (long long)(g.L[3] - 1) * d : s - d;
+        const float tb = (float)g.tbc;
+        hop_dir2<3, -1>(a0, a1, in0, in1, Uout, s, nf, st, last ? tb : 1.0f);
+        hop_dir2<3, +1>(a0, a1, in0, in1, Uin, nb, nb, st, first ? tb : 1.0f);
+    }
+    cx<float> v[12], x[12];
+    if (MODE == HOP_K1) {
+#pragma unroll
+        for (int i = 0; i < 12; i++) a0[i] = -0.5f * a0[i];
+        clover_apply<float>(clov, st, s, a0, v);
+        store_spinor(out0, st, s, v);
+        if (two) {
+#pragma unroll
+            for (int i = 0; i < 12; i++) a1[i] = -0.5f * a1[i];
+            clover_apply<float>(clov, st, s, a1, v);
+            store_spinor(out1, st, s, v);
+        }
+    } else {   // HOP_K2
+        load_spinor_rw(in20, st, s, x);
+        clover_apply<float>(clov, st, s, x, v);
+#pragma unroll
+        for (int i = 0; i < 12; i++) v[i] = v[i] + 0.5f * a0[i];
+        store_spinor(out0, st, s, v);
+        if (two) {
+            load_spinor_rw(in21, st, s, x);
+            clover_apply<float>(clov, st, s, x, v);
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = v[i] + 0.5f * a1[i];
+            store_spinor(out1, st, s, v);
+        }
+    }
+}
+
 template <typename R, int MODE>
 __global__ void LQ_HOP_BOUNDS hop_kernel(Geom g, HopArgs<R> k)
 {
@@ -228,7 +313,7 @@ static void launch_hop_bf(const Exec &e, const HopCall &c)
 #else
 #define LQ_GROUP_BOUNDS __launch_bounds__(LQ_HOP_THREADS)
 #endif
-template <int MODE>
+template <int MODE, int RPT>
 __global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
                                                                    const int4 *__restrict__ tiles, int ntiles,
                                                                    const float4 *in, const float4 *in2, float4 *out)
@@ -239,12 +324,20 @@ __global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
         const LatDesc *L = d + w.x;
         const Geom g = L->g;
         const long long s = (long long)w.y * blockDim.x + threadIdx.x;
-        const int r = w.z + threadIdx.y;
+        const int r = w.z + RPT * threadIdx.y;   // the thread's first right-hand side
         if (s >= g.Vh || r >= L->nrhs) continue;
         const Coords c = cb_coords(g, s, pout);
         const long long o = L->off + r * L->fs;
-        hop_body<float, MODE>(g, L->U[pout], L->U[1 - pout], L->clov[pout], 0.0f, in + o,
-                              in2 ? in2 + o : nullptr, (const float4 *)nullptr, out + o, s, c);
+        if (RPT == 1) {
+            hop_body<float, MODE>(g, L->U[pout], L->U[1 - pout], L->clov[pout], 0.0f, in + o,
+                                  in2 ? in2 + o : nullptr, (const float4 *)nullptr, out + o, s, c);
+        } else {
+            // the second right-hand side, when it exists (else the first is read twice, stored once)
+            const bool two = r + 1 < L->nrhs;
+            const long long o1 = two ? o + L->fs : o;
+            hop_body2<MODE>(g, L->U[pout], L->U[1 - pout], L->clov[pout], in + o, in + o1,
+                            in2 ? in2 + o : nullptr, in2 ? in2 + o1 : nullptr, out + o, out + o1, two, s, c);
+        }
     }
 }
 
@@ -489,26 +582,31 @@ static const double c_hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 
 double hop_bytes(int mode, int prec, int nrhs, double sites) { return sites * hop_site_bytes(mode, prec, nrhs); }
 double hop_flops(int mode, double site_rhs) { return site_rhs * c_hop_flops[mode]; }
 
-int hop_group_resident()
+int hop_group_resident(int rpt)
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_group_kernel<HOP_K1>, LQ_HOP_THREADS, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_group_kernel<HOP_K2>, LQ_HOP_THREADS, 0);
+    if (rpt == 2) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_group_kernel<HOP_K1, 2>, LQ_HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_group_kernel<HOP_K2, 2>, LQ_HOP_THREADS, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_group_kernel<HOP_K1, 1>, LQ_HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_group_kernel<HOP_K2, 1>, LQ_HOP_THREADS, 0);
+    }
     const int r = a < b ? a : b;
     return r < 1 ? 1 : r;
 }
 
 void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, int ntiles, int grid, int spt,
-               const void *in, const void *in2, void *out, double bytes, double flops)
+               int rpt, const void *in, const void *in2, void *out, double bytes, double flops)
 {
     Launch L_(e, mode == HOP_K1 ? K_HOP_K1_F32 : K_HOP_K2_F32, bytes, flops);
     const dim3 block(spt, LQ_HOP_THREADS / spt);
-    if (mode == HOP_K1)
-        hop_group_kernel<HOP_K1><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, (const float4 *)in,
-                                                            (const float4 *)in2, (float4 *)out);
-    else
-        hop_group_kernel<HOP_K2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, (const float4 *)in,
-                                                            (const float4 *)in2, (float4 *)out);
+    const float4 *i1 = (const float4 *)in, *i2 = (const float4 *)in2;
+    float4 *o = (float4 *)out;
+    if (mode == HOP_K1 && rpt == 2) hop_group_kernel<HOP_K1, 2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+    else if (mode == HOP_K1) hop_group_kernel<HOP_K1, 1><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+    else if (rpt == 2) hop_group_kernel<HOP_K2, 2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+    else hop_group_kernel<HOP_K2, 1><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
 }
 
 void hop(const Exec &e, const HopCall &c)

@@ -180,14 +180,16 @@ struct LatDesc {
 };
 // threads per block of the hopping kernels
 constexpr int kHopBlock = 128;
-// resident blocks per SM of the batched hopping kernel (for a persistent grid)
-int hop_group_resident();
+// resident blocks per SM of the batched hopping kernel with rpt (1 or 2)
+// right-hand sides per thread (for a persistent grid)
+int hop_group_resident(int rpt);
 // One work-table entry of the batched hopping launch: lattice, site block (of
-// blockDim.x sites) and first right-hand side (of blockDim.y).
+// blockDim.x sites) and first right-hand side (of rpt * blockDim.y, rpt
+// right-hand sides per thread sharing each link load).
 // A persistent grid of `grid` blocks of (spt, kHopBlock / spt) threads
 // walks the table; mode HOP_K1 (odd output) or HOP_K2 (even output), FP32.
 void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, int ntiles, int grid, int spt,
-               const void *in, const void *in2, void *out, double bytes, double flops);
+               int rpt, const void *in, const void *in2, void *out, double bytes, double flops);
 // FP32 hopping-launch byte and flop counts of `sites` output sites with nrhs
 // right-hand sides sharing links and clover
 double hop_bytes(int mode, int prec, int nrhs, double sites);

@@ -261,8 +261,8 @@ _lib.lq_solve_group.restype = ctypes.c_int
 _lib.lq_group_set_autotune.argtypes = [_P, ctypes.c_int]
 _lib.lq_group_set_autotune.restype = ctypes.c_int
 _lib.lq_group_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(ctypes.c_double)]
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
 _lib.lq_group_tuning.restype = ctypes.c_int
 
 
@@ -299,13 +299,22 @@ def lq_group_set_autotune(grp, on: bool) -> None:
     _check(None, _lib.lq_group_set_autotune(grp, int(bool(on))))
 
 
+_lib.lq_group_set_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+_lib.lq_group_set_shape.restype = ctypes.c_int
+
+
+def lq_group_set_shape(grp, sites_per_tile: int, rhs_per_thread: int, grid_factor: int) -> None:
+    _check(None, _lib.lq_group_set_shape(grp, int(sites_per_tile), int(rhs_per_thread), int(grid_factor)))
+
+
 def lq_group_tuning(grp):
-    """(sites per tile, grid, BLAS blocks per system, hop ms, BLAS ms) in use."""
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    """(sites per tile, right-hand sides per thread, grid, BLAS blocks per
+    system, hop ms, BLAS ms) in use."""
+    a, r, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     d, e = ctypes.c_double(), ctypes.c_double()
-    _check(None, _lib.lq_group_tuning(grp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
-                                      ctypes.byref(e)))
-    return a.value, b.value, c.value, d.value, e.value
+    _check(None, _lib.lq_group_tuning(grp, ctypes.byref(a), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c),
+                                      ctypes.byref(d), ctypes.byref(e)))
+    return a.value, r.value, b.value, c.value, d.value, e.value
 
 
 def make_batch_params(tol=1e-10, restart=8, max_restarts=10, smooth_n=16, smooth_tol=1e-5) -> lq_solver_params:

@@ -61,7 +61,7 @@ def main():
         out = max(s.rel_resid_true for s in st)
         print("outer corrections", [s.iters for s in st], "inner steps", [s.inner_iters for s in st],
               "ms", round(st[0].time_ms, 2))
-        print("tuning (sites/tile, grid, blas blocks, hop pair ms, blas pair ms)", lqdd.lq_group_tuning(grp))
+        print("tuning (sites/tile, rhs/thread, grid, blas blocks, hop pair ms, blas pair ms)", lqdd.lq_group_tuning(grp))
         lqdd.lq_group_destroy(grp)
     elif a.mode == "sap":
         r = torch.from_numpy(synth.gaussian_spinor(V, 2003)).cuda()

@@ -130,12 +130,24 @@ def test_solve_group_uneven_lattices():
                     assert r_true <= 2e-10, (p.L, r, r_true)
                     assert abs(r_true - stats[k].rel_resid_true) <= 1e-3 * r_true + 1e-15
                     k += 1
-            spt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
-            assert spt in (16, 32, 64, 128) and grid >= 1 and blas >= 1
+            spt, rpt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
+            assert spt in (16, 32, 64, 128) and rpt in (1, 2) and grid >= 1 and blas >= 1
             if autotune:
                 assert hop_ms > 0 and blas_ms > 0
             else:
-                assert (spt, hop_ms, blas_ms) == (32, 0.0, 0.0)
+                assert (spt, rpt, hop_ms, blas_ms) == (32, 1, 0.0, 0.0)
+        # every pinned launch shape (two right-hand sides per thread with odd counts
+        # included) gives converged solutions
+        for spt, rpt, fac in [(32, 2, 1), (128, 2, 0), (16, 1, 2), (64, 2, 2)]:
+            lqdd.lq_group_set_shape(grp, spt, rpt, fac)
+            xs2 = [p.torch.zeros_like(d) for p, d in zip(pairs, db)]
+            status, stats = lqdd.lq_solve_group(grp, pairs[0].ctx, lqdd.make_batch_params(tol=1e-10), db, xs2)
+            assert status == lqdd.LQ_OK
+            assert lqdd.lq_group_tuning(grp)[:2] == (spt, rpt)
+            for p, b, x in zip(pairs, bs, xs2):
+                xh = p.host(x)
+                for r in range(b.shape[0]):
+                    assert np.linalg.norm(b[r] - p.lat.dirac(xh[r])) / np.linalg.norm(b[r]) <= 2e-10
         # the same systems one member at a time (lq_solve_batch) give the same solutions
         for p, d, x in zip(pairs, db, xs):
             x1 = p.torch.zeros_like(d)
