@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-sap", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-48x96", action="store_true")
     return ap.parse_args()
 
 
@@ -369,6 +370,60 @@ def run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks, V, omega):
     return res
 
 
+def run_48x96(lqdd, synth, torch, stream, dev, pk):
+    """The 48^3 x 96 workload (eps 0.2, m0 0.01, c_sw 1, antiperiodic t, link
+    seed 1002, Gaussian source seed 2002): the FP32 D_S apply against the
+    measured HBM bandwidth, and the mixed solve against plain FP64 GMRES(30),
+    both to 1e-10 on the true residual."""
+    import numpy as np
+    L = (48, 48, 48, 96)
+    V = int(np.prod(L))
+    ctx = lqdd.lq_create(lqdd.make_lattice(L, TBC, 0.01, CSW), stream.cuda_stream)
+    try:
+        lqdd.lq_set_gauge(ctx, torch.from_numpy(synth.gauge_links(L, 0.2, 1002)).to(dev))
+        b = torch.from_numpy(synth.gaussian_spinor(V, 2002)).to(dev)
+        xe = b[:V // 2].contiguous()
+        ye = torch.empty_like(xe)
+        res = {"lattice": list(L)}
+        for prec, name in ((lqdd.LQ_F32, "f32"), (lqdd.LQ_F64, "f64")):
+            lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
+            lqdd.lq_profile(ctx, 1)
+            for _ in range(10):
+                lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
+            prof = read_profile(lqdd, ctx)
+            lqdd.lq_profile(ctx, 0)
+            k1, k2 = f"hop_k1_{name}", f"hop_k2_{name}"
+            ms = (prof[k1]["ms"] + prof[k2]["ms"]) / 10
+            by = (prof[k1]["bytes"] + prof[k2]["bytes"]) / 10
+            res[f"ds_{name}"] = {"us": round(1e3 * ms, 1), "gbs": round(by / (ms / 1e3) / 1e9, 1),
+                                 "hbm_frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
+        x = torch.zeros_like(b)
+        mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                                 max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
+                                 smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+        fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
+        for name, prm, reps in (("mixed", mixed, 3), ("fp64", fp64, 1)):
+            x.zero_()
+            lqdd.lq_solve(ctx, prm, b, x)
+            ts = []
+            for _ in range(reps):
+                x.zero_()
+                torch.cuda.synchronize()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                status, st = lqdd.lq_solve(ctx, prm, b, x)
+                z.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(z))
+            res[f"{name}_ms"] = round(sorted(ts)[len(ts) // 2], 2)
+            res[name] = {"iters": st.iters, "inner_iters": st.inner_iters, "rel_resid_true": st.rel_resid_true,
+                         "status": lqdd.lq_status_string(status)}
+        res["speedup"] = round(res["fp64_ms"] / res["mixed_ms"], 2)
+        return res
+    finally:
+        lqdd.lq_destroy(ctx)
+
+
 def run_bf16(lqdd, torch, stream, ctx, db, x, pk, V, omega):
     """BF16 storage on the benchmark lattice: the D_S apply (1200 algorithmic
     bytes per site) against FP32 (1824), its relative error against the FP64
@@ -601,6 +656,10 @@ def run_ours(args):
     if not args.no_batch:
         batched = run_batched(lqdd, synth, torch, stream, dev)
 
+    big = None
+    if not args.no_48x96 and world == 1:
+        big = run_48x96(lqdd, synth, torch, stream, dev, peaks())
+
     force = None
     if not args.no_force:
         force = run_force(lqdd, synth, torch, stream, dev, peaks())
@@ -682,6 +741,7 @@ def run_ours(args):
         "force": force,
         "sap": sap,
         "bf16": bf16,
+        "lattice_48x96": big,
         "kernels": prof,
         "step_bytes": step_bytes,
     }

@@ -216,6 +216,37 @@ def test_full_size_sampled_schur(lqdd):
         p.close()
 
 
+def test_full_size_48x96_sampled_schur_and_mixed_solve(lqdd):
+    """48^3 x 96 (eps = 0.2, m0 = 0.01, csw = 1): D_S in FP64, FP32 and df64 on
+    the full lattice at sampled even sites against the oracle's site-by-site
+    Eq. 3, and the mixed solve (FGMRES(10) df64 / GMRES(8) FP32) to 1e-10, its
+    residual recomputed with the FP64 operator checked above."""
+    L = (48, 48, 48, 96)
+    p = Pair(L, eps=0.2, seed=1002, m0=0.01, csw=1.0)
+    try:
+        xe = synth.gaussian_spinor(p.Vh, 2002)
+        rng = np.random.default_rng(1)
+        sel = np.unique(np.concatenate([[0, 1, p.Vh - 1, p.Vh // 3], rng.integers(0, p.Vh, 40)]))
+        ref = p.lat.schur_sites(xe, sel)
+        for prec in (0, 1, 2):
+            y = p.apply(lqdd.LQ_OP_SCHUR, prec, xe)
+            assert rel(y[sel], ref) < TOL[prec]
+        torch = p.torch
+        b = torch.from_numpy(synth.gaussian_spinor(p.V, 2003)).cuda()
+        x = torch.zeros_like(b)
+        prm = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                               max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
+                               smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+        status, st = lqdd.lq_solve(p.ctx, prm, b, x)
+        assert status == lqdd.LQ_OK
+        Dx = torch.empty_like(b)
+        lqdd.lq_apply(p.ctx, lqdd.LQ_OP_FULL, lqdd.LQ_F64, x, Dx)
+        r = float(torch.linalg.vector_norm(b - Dx) / torch.linalg.vector_norm(b))
+        assert r <= 1e-10 and abs(r - st.rel_resid_true) < 1e-2 * r
+    finally:
+        p.close()
+
+
 # ---- status codes and failure handling (host-visible, nothing faults) -------------
 
 def test_status_codes(lqdd):
