@@ -1267,17 +1267,15 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
             for (int p = 0; p < 2; p++) c->U16[p] = dev_alloc(c, (size_t)4 * 3 * g.stride * 8);
         }
         c->have_gauge = false;
-        // links in all three precisions; clover and inverse built in df64 and
-        // rounded to the FP64 and FP32 copies
+        // links in every precision; clover and inverse built in df64, their
+        // FP64 and FP32 copies rounded by the same kernels
         import_links(e, U, c->U64, c->U32, c->Udf);
         for (int p = 0; p < 2; p++) links_to_bf16(e, c->U32[p], c->U16[p]);
         const void *udf[2] = {c->Udf[0], c->Udf[1]};
-        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
+        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C64, c->C32,
+                     ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
-        clover_invert(e, c->Cdf[1], c->Cidf, c->dflag);
-        clover_round(e, c->Cdf[0], c->C64[0], c->C32[0]);
-        clover_round(e, c->Cdf[1], c->C64[1], c->C32[1]);
-        clover_round(e, c->Cidf, c->Ci64, c->Ci32);
+        clover_invert(e, c->Cdf[1], c->Cidf, c->Ci64, c->Ci32, c->dflag);
         ck_launch(c, "set_gauge kernels");
         int flag = 0;
         ck(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "cudaMemcpyAsync");

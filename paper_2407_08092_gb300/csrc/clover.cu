@@ -13,8 +13,8 @@
 // g_4 = [[0,1],[1,0]].
 //
 // The library builds and inverts in df64 (FP64-accurate, on the FP32 units,
-// which GB300 runs at 64 times its FP64 rate) and derives the FP64 and FP32
-// copies by rounding.  The build is split in two launches: one thread per
+// which GB300 runs at 64 times its FP64 rate); the assembly and inverse kernels
+// also write the FP64 and FP32 copies, rounded from df64.  The build is split in two launches: one thread per
 // (site, plane) computes the four leaves and F of that plane into a scratch
 // array, then one thread per site assembles the two 6x6 blocks.
 #include "leaves.cuh"
@@ -23,6 +23,24 @@
 namespace lq {
 
 __device__ __forceinline__ void store_pair(double2 *p, double a, double b) { *p = make_double2(a, b); }
+
+// one packed 6x6 block (36 df64 reals) of the site with checkerboard index s:
+// the df64 copy and its rounding to FP64 and FP32 (FP32: two complex slots per
+// float4)
+__device__ __forceinline__ void store_block_all(const Geom &g, int b, long long s, const df64 r[36], df2 *Cdf,
+                                                double2 *C64, float4 *C32)
+{
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const df64 a0 = r[4 * k], a1 = r[4 * k + 1], a2 = r[4 * k + 2], a3 = r[4 * k + 3];
+        Cdf[(b * 18 + 2 * k) * g.stride + s] = df2{a0.hi, a0.lo, a1.hi, a1.lo};
+        Cdf[(b * 18 + 2 * k + 1) * g.stride + s] = df2{a2.hi, a2.lo, a3.hi, a3.lo};
+        const double d0 = df_to_double(a0), d1 = df_to_double(a1), d2 = df_to_double(a2), d3 = df_to_double(a3);
+        C64[(b * 18 + 2 * k) * g.stride + s] = make_double2(d0, d1);
+        C64[(b * 18 + 2 * k + 1) * g.stride + s] = make_double2(d2, d3);
+        C32[(b * 9 + k) * g.stride + s] = make_float4((float)d0, (float)d1, (float)d2, (float)d3);
+    }
+}
 __device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.hi, a.lo, b.hi, b.lo}; }
 __device__ __forceinline__ bool positive(double d) { return d > 0.0; }
 __device__ __forceinline__ bool positive(df64 d) { return df_positive(d); }
@@ -114,7 +132,8 @@ __device__ __forceinline__ cx<df64> f_entry(const float2 *__restrict__ Fb, long 
 // block b: G1 = -F_yz +- F_xt, G2 = F_xz +- F_yt, G3 = -F_xy +- F_zt (+ for b = 0),
 // M = i h [[G3, G1 - i G2], [G1 + i G2, -G3]], h = c_sw / 2, C = (4 + m0) + M.
 __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const float2 *__restrict__ Fb, double csw,
-                                                              double m0, df2 *Ce, df2 *Co)
+                                                              double m0, df2 *Ce, df2 *Co, double2 *C64e,
+                                                              double2 *C64o, float4 *C32e, float4 *C32o)
 {
     const long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (lex >= g.V) return;
@@ -159,8 +178,7 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
                 out[k] = m.re;
                 out[k + 1] = m.im;
             }
-#pragma unroll
-        for (int k = 0; k < 18; k++) store_pair(C + (b * 18 + k) * g.stride + cb, out[2 * k], out[2 * k + 1]);
+        store_block_all(g, b, cb, out, C, parity ? C64o : C64e, parity ? C32o : C32e);
     }
 }
 
@@ -168,7 +186,8 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
 // A = L D L^+ (L unit lower, D real); A^{-1} = L^{-+} D^{-1} L^{-1}.
 template <typename R>
 __global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const typename St<R>::vec *__restrict__ C,
-                                                            typename St<R>::vec *Ci, int *flag)
+                                                            typename St<R>::vec *Ci, double2 *Ci64, float4 *Ci32,
+                                                            int *flag)
 {
     long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 2 * g.Vh) return;
@@ -221,26 +240,8 @@ __global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const typena
             out[kk] = acc.re;
             out[kk + 1] = acc.im;
         }
-    for (int k = 0; k < 18; k++) store_pair(Ci + (b * 18 + k) * g.stride + s, out[2 * k], out[2 * k + 1]);
+    store_block_all(g, b, s, out, Ci, Ci64, Ci32);
     if (bad) atomicAdd(flag, 1);
-}
-
-// df64 packed blocks of one parity -> FP64 and FP32 copies (rounding)
-__global__ void clover_round_kernel(Geom g, const df2 *__restrict__ Cdf, double2 *C64, float4 *C32)
-{
-    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (id >= 2 * g.Vh) return;
-    const int b = (int)(id / g.Vh);
-    const long long s = id - b * g.Vh;
-    for (int k = 0; k < 9; k++) {
-        const df2 u = Cdf[(b * 18 + 2 * k) * g.stride + s];
-        const df2 v = Cdf[(b * 18 + 2 * k + 1) * g.stride + s];
-        const double2 du = make_double2((double)u.rh + (double)u.rl, (double)u.ih + (double)u.il);
-        const double2 dv = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
-        C64[(b * 18 + 2 * k) * g.stride + s] = du;
-        C64[(b * 18 + 2 * k + 1) * g.stride + s] = dv;
-        C32[(b * 9 + k) * g.stride + s] = make_float4((float)du.x, (float)du.y, (float)dv.x, (float)dv.y);
-    }
 }
 
 __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, const double2 *__restrict__ Co,
@@ -276,7 +277,8 @@ __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, con
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *Fscratch)
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C64[2],
+                  void *C32[2], void *Fscratch)
 {
     {
         // unique bytes per site: its four df64 links (4 x 144) and the six F
@@ -287,23 +289,18 @@ void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void
                                                                                 (const df2 *)Udf[1],
                                                                                 (float2 *)Fscratch);
     }
-    Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * 8));
-    clover_assemble_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(e.g, (const float2 *)Fscratch, csw, m0,
-                                                                     (df2 *)Cdf[0], (df2 *)Cdf[1]);
+    // reads the six F, writes the blocks in df64, FP64 and FP32
+    Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * (8 + 8 + 4)));
+    clover_assemble_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(
+        e.g, (const float2 *)Fscratch, csw, m0, (df2 *)Cdf[0], (df2 *)Cdf[1], (double2 *)C64[0],
+        (double2 *)C64[1], (float4 *)C32[0], (float4 *)C32[1]);
 }
 
-void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag)
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci64, void *Ci32, int *flag)
 {
-    Launch L_(e, K_CLOVER, (double)e.g.Vh * 2 * 72 * 8, (double)e.g.Vh * 2 * 1500);
-    clover_invert_kernel<df64><<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(e.g, (const df2 *)Cdf,
-                                                                              (df2 *)Cidf, flag);
-}
-
-void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32)
-{
-    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 8 + 4));
-    clover_round_kernel<<<blocks_for(2 * e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const df2 *)Cdf, (double2 *)C64,
-                                                                      (float4 *)C32);
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 8 + 8 + 4), (double)e.g.Vh * 2 * 1500);
+    clover_invert_kernel<df64><<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(
+        e.g, (const df2 *)Cdf, (df2 *)Cidf, (double2 *)Ci64, (float4 *)Ci32, flag);
 }
 
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out)

@@ -252,22 +252,6 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS, 6) hop_kernel_occ(Geom g, HopA
     hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(LQ_HOP_THREADS) hop_kernel_multi(Geom g, HopArgs<R> k)
-{
-    // block = 32 consecutive sites (x) for MRHS_PER_BLOCK right-hand sides (y);
-    // consecutive blocks cover the right-hand-side groups of the same sites, so
-    // a site's links and clover block reach L1/L2 once for all of them
-    const int groups = (k.nrhs + blockDim.y - 1) / blockDim.y;
-    const long long sb = blockIdx.x / groups;
-    const int r = (blockIdx.x - sb * groups) * blockDim.y + threadIdx.y;
-    const long long s = sb * 32 + threadIdx.x;
-    if (s >= g.Vh || r >= k.nrhs) return;
-    const Coords c = cb_coords(g, s, k.pout);
-    const long long o = r * k.fs;
-    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in + o, k.in2 ? k.in2 + o : nullptr,
-                      k.b ? k.b + o : nullptr, k.out + o, s, c);
-}
 
 // BF16 spinors and links, FP32 clover and arithmetic (all modes)
 struct HopArgsBF {
@@ -531,18 +515,22 @@ static void launch_hop(const Exec &e, const HopCall &c)
     const unsigned blocks = (unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS);
     if constexpr (std::is_same<R, df64>::value)
         hop_df_kernel<MODE><<<blocks, 128, 0, e.st>>>(e.g, k);
-    else if (c.nrhs > 1)
-    {
-        const int rpb = LQ_HOP_THREADS / 32;   // right-hand sides per block
-        const long long sblocks = (e.g.Vh + 31) / 32, groups = (c.nrhs + rpb - 1) / rpb;
-        hop_kernel_multi<R, MODE><<<(unsigned)(sblocks * groups), dim3(32, rpb), 0, e.st>>>(e.g, k);
-    }
     else
     {
-        if constexpr (std::is_same<R, float>::value && (MODE == HOP_K2 || MODE == HOP_RICH))
-            hop_kernel_occ<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
-        else
-            hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
+        // several right-hand sides of FP64 or FP32 fields: one launch each (the
+        // batched FP32 solve uses the work-table kernel instead)
+        for (int r = 0; r < c.nrhs; r++) {
+            HopArgs<R> kr = k;
+            const long long o = r * k.fs;
+            kr.in = k.in + o;
+            kr.in2 = k.in2 ? k.in2 + o : nullptr;
+            kr.b = k.b ? k.b + o : nullptr;
+            kr.out = k.out + o;
+            if constexpr (std::is_same<R, float>::value && (MODE == HOP_K2 || MODE == HOP_RICH))
+                hop_kernel_occ<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, kr);
+            else
+                hop_kernel<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, kr);
+        }
     }
 }
 
@@ -618,8 +606,11 @@ void hop(const Exec &e, const HopCall &c)
         else if (c.prec == P16) launch_hop_bf<M>(e, c);                         \
         else launch_hop<df64, M>(e, c);                                         \
         break;
-    Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * hop_site_bytes(c.mode, c.prec, c.nrhs),
-              (double)e.g.Vh * c_hop_flops[c.mode] * c.nrhs);
+    // df64 keeps the right-hand sides of a site in one thread (links and clover
+    // counted once); FP64 and FP32 launch once per right-hand side
+    const double site_bytes = c.prec == PDF ? hop_site_bytes(c.mode, c.prec, c.nrhs)
+                                            : c.nrhs * hop_site_bytes(c.mode, c.prec, 1);
+    Launch L_(e, hop_class(c.mode, c.prec), (double)e.g.Vh * site_bytes, (double)e.g.Vh * c_hop_flops[c.mode] * c.nrhs);
     switch (c.mode) {
         LQ_CASE(HOP_K1)
         LQ_CASE(HOP_K2)

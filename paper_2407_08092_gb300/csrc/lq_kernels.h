@@ -105,13 +105,14 @@ void convert(const Exec &e, int from, const void *in, int to, void *out);
 void gamma5(const Exec &e, int prec, const void *in, void *out);
 
 // ---- clover (clover.cu) ----------------------------------------------------
-// C(x) of every site from the internal df64 links, df64 packed blocks per parity;
-// Fscratch: device scratch of 6 * 9 * V * 8 bytes (the six field strengths)
-void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *Fscratch);
-// df64 packed inverse of the blocks of one parity by LDL^+; *flag += failures
-void clover_invert(const Exec &e, const void *Cdf, void *Cidf, int *flag);
-// df64 packed blocks of one parity -> rounded FP64 and FP32 copies
-void clover_round(const Exec &e, const void *Cdf, void *C64, void *C32);
+// C(x) of every site from the internal df64 links: packed blocks per parity in
+// df64 and, rounded, FP64 and FP32; Fscratch: device scratch of 6 * 9 * V * 8
+// bytes (the six field strengths)
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C64[2],
+                  void *C32[2], void *Fscratch);
+// inverse of the blocks of one parity by LDL^+ in df64, written in df64, FP64
+// and FP32; *flag += failures
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci64, void *Ci32, int *flag);
 // natural export: out[V][2][6][6] c128 from FP64 packed blocks (null parity pointer -> zeros)
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
 
