@@ -236,7 +236,11 @@ __global__ void LQ_HOP_BOUNDS hop_kernel(Geom g, HopArgs<R> k)
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
     const Coords c = cb_coords(g, s, k.pout);
-    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+    if constexpr (std::is_same<R, float>::value)   // links and clover read once: no L1 allocation
+        hop_body<R, MODE>(g, (const F4S *)k.Uout, (const F4S *)k.Uin, (const F4S *)k.clov, k.omega, k.in, k.in2,
+                          k.b, k.out, s, c);
+    else
+        hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
 }
 
 // The same for FP32 K2 and its Richardson form, asked to fit six blocks per SM
@@ -249,7 +253,8 @@ __global__ void __launch_bounds__(LQ_HOP_THREADS, 6) hop_kernel_occ(Geom g, HopA
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
     const Coords c = cb_coords(g, s, k.pout);
-    hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+    hop_body<R, MODE>(g, (const F4S *)k.Uout, (const F4S *)k.Uin, (const F4S *)k.clov, k.omega, k.in, k.in2, k.b,
+                      k.out, s, c);
 }
 
 
