@@ -36,9 +36,12 @@ __device__ __forceinline__ BfS4 ldg(const BfS4 *p)
     const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
     return *reinterpret_cast<const BfS4 *>(&t);
 }
+// BF16 links are read once per launch: loaded without L1 allocation, like the
+// FP32 links of the single-right-hand-side kernels
 __device__ __forceinline__ BfL2 ldg(const BfL2 *p)
 {
-    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    uint2 t;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(t.x), "=r"(t.y) : "l"(p));
     return *reinterpret_cast<const BfL2 *>(&t);
 }
 

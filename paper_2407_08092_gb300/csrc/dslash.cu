@@ -263,7 +263,7 @@ struct HopArgsBF {
     const BfS4 *in, *in2, *b;
     BfS4 *out;
     const BfL2 *Uout, *Uin;
-    const float4 *clov;
+    const F4S *clov;   // FP32 clover blocks, read once
     float omega;
     int pout;
 };
@@ -286,7 +286,7 @@ static void launch_hop_bf(const Exec &e, const HopCall &c)
     k.out = (BfS4 *)c.out;
     k.Uout = (const BfL2 *)c.U[c.pout];
     k.Uin = (const BfL2 *)c.U[1 - c.pout];
-    k.clov = (const float4 *)c.clov;
+    k.clov = (const F4S *)c.clov;
     k.omega = (float)c.omega;
     k.pout = c.pout;
     hop_kernel_bf<MODE><<<(unsigned)((e.g.Vh + LQ_HOP_THREADS - 1) / LQ_HOP_THREADS), LQ_HOP_THREADS, 0, e.st>>>(e.g, k);
