@@ -134,10 +134,18 @@ __device__ __forceinline__ void sap_sum3(float v[3], float *sh)
 }
 
 // The CTA asks for three resident blocks per SM (at most 168 registers); the
-// MR iterate and residual live in shared memory, not in registers.
+// MR iterate and residual live in shared memory, not in registers.  The solve
+// is one loop over half-steps, each one block hop into one parity followed by
+// its epilogue, so that a single copy of the hop code serves all of them (the
+// instruction cache holds it):
+//   0      odd:  D_oo^{-1} r_o                               (no hop)
+//   1      even: r_hat = r_e + 1/2 H_eo (D_oo^{-1} r_o); e = 0
+//   2j+2   odd:  t = D_oo^{-1} (-1/2 H_oe res)               (MR step j)
+//   2j+3   even: p = C res + 1/2 H_eo t; alpha; e += alpha res; res -= alpha p
+//   2m+2   odd:  e_o = D_oo^{-1} (r_o + 1/2 H_oe e_e); x += e
 __global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
 {
-    __shared__ float2 smE[12 * SAP_THREADS];   // even: r_hat, then the MR residual, then e_e for the odd update
+    __shared__ float2 smE[12 * SAP_THREADS];   // even: r_hat, then the MR residual
     __shared__ float2 smX[12 * SAP_THREADS];   // even: the MR iterate e_e
     __shared__ float2 smO[12 * SAP_THREADS];   // odd: D_oo^{-1} r_o, then t_o
     __shared__ float red[3 * (SAP_THREADS / 32)];
@@ -145,102 +153,95 @@ __global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
     const bool on = i < a.bvh;
     const int4 o4 = a.origin[blockIdx.x];
     const int O[4] = {o4.x, o4.y, o4.z, o4.w};
-    int le[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, Ge[4], Go[4];
-    long long cbe = 0, cbo = 0;
+    int le[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
     if (on) {
         sap_local(a, i, 0, le);
         sap_local(a, i, 1, lo);
     }
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        Ge[mu] = O[mu] + le[mu];
-        Go[mu] = O[mu] + lo[mu];
-    }
-    if (on) {
-        cbe = sap_global_cb(a.g, Ge);
-        cbo = sap_global_cb(a.g, Go);
-    }
     const long long st = a.g.stride;
-    cx<float> v[12], w[12];
-
-    // D_oo^{-1} r_o on the odd sites
-    if (on) {
-        load_spinor(a.r[1], st, cbo, v);
-        clover_apply<float>(a.Ci, st, cbo, v, w);
-        st_sm(smO, i, w);
-    }
-    __syncthreads();
-    // r_hat_e = r_e - D_eo D_oo^{-1} r_o = r_e + 1/2 H_eo (D_oo^{-1} r_o); e_e = 0
-    if (on) {
-        load_spinor(a.r[0], st, cbe, v);
-        sap_hop(a, smO, le, Ge, 0, cbe, w);
+    const int last = 2 * a.m + 2;
+#pragma unroll 1
+    for (int ph = 0; ph <= last; ph++) {
+        const int p = (ph == 1 || (ph > 1 && ph < last && (ph & 1))) ? 0 : 1;   // output parity
+        int l[4], G[4];
 #pragma unroll
-        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
-        st_sm(smE, i, v);
-#pragma unroll
-        for (int k = 0; k < 12; k++) w[k] = {0.0f, 0.0f};
-        st_sm(smX, i, w);
-    }
-    __syncthreads();
-
-    // Minimal Residual on S: p = S res, alpha = (p, res) / (p, p), e += alpha res, res -= alpha p
-    for (int j = 0; j < a.m; j++) {
-        // t_o = D_oo^{-1} (-1/2 H_oe res)
-        if (on) {
-            sap_hop(a, smE, lo, Go, 1, cbo, v);
-#pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = -0.5f * v[k];
-            clover_apply<float>(a.Ci, st, cbo, v, w);
-            st_sm(smO, i, w);
+        for (int mu = 0; mu < 4; mu++) {
+            l[mu] = p ? lo[mu] : le[mu];
+            G[mu] = O[mu] + l[mu];
         }
-        __syncthreads();
-        // p = C res + 1/2 H_eo t_o
+        const long long cb = on ? sap_global_cb(a.g, G) : 0;
+        cx<float> w[12];
+        if (on && ph > 0) sap_hop(a, p ? (ph == last ? smX : smE) : smO, l, G, p, cb, w);
         float d[3] = {0.0f, 0.0f, 0.0f};
         cx<float> pv[12];
         if (on) {
-            ld_sm(smE, i, v);
-            clover_apply<float>(a.Ce, st, cbe, v, pv);
-            sap_hop(a, smO, le, Ge, 0, cbe, w);
+            cx<float> v[12];
+            if (p == 1) {   // odd output: D_oo^{-1} (...)
+                if (ph == 0 || ph == last) {
+                    load_spinor(a.r[1], st, cb, v);
+                    if (ph == last) {
 #pragma unroll
-            for (int k = 0; k < 12; k++) {
-                pv[k] = pv[k] + 0.5f * w[k];
-                d[0] = fmaf(pv[k].re, v[k].re, fmaf(pv[k].im, v[k].im, d[0]));    // Re (p, res)
-                d[1] = fmaf(pv[k].re, v[k].im, fmaf(-pv[k].im, v[k].re, d[1]));   // Im (p, res)
-                d[2] = fmaf(pv[k].re, pv[k].re, fmaf(pv[k].im, pv[k].im, d[2]));  // (p, p)
+                        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = -0.5f * w[k];
+                }
+                clover_apply<float>(a.Ci, st, cb, v, pv);
+                if (ph < last) {
+                    st_sm(smO, i, pv);
+                } else {   // x += e on both parities of the site pair
+                    load_spinor_rw(a.x[1], st, cb, v);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = v[k] + pv[k];
+                    store_spinor(a.x[1], st, cb, v);
+                    int Ge[4];
+#pragma unroll
+                    for (int mu = 0; mu < 4; mu++) Ge[mu] = O[mu] + le[mu];
+                    const long long cbe = sap_global_cb(a.g, Ge);
+                    ld_sm(smX, i, pv);
+                    load_spinor_rw(a.x[0], st, cbe, v);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = v[k] + pv[k];
+                    store_spinor(a.x[0], st, cbe, v);
+                }
+            } else if (ph == 1) {   // r_hat = r_e + 1/2 H_eo (D_oo^{-1} r_o), e = 0
+                load_spinor(a.r[0], st, cb, v);
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
+                st_sm(smE, i, v);
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = {0.0f, 0.0f};
+                st_sm(smX, i, v);
+            } else {   // p = C res + 1/2 H_eo t and the dot products
+                ld_sm(smE, i, v);
+                clover_apply<float>(a.Ce, st, cb, v, pv);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    pv[k] = pv[k] + 0.5f * w[k];
+                    d[0] = fmaf(pv[k].re, v[k].re, fmaf(pv[k].im, v[k].im, d[0]));    // Re (p, res)
+                    d[1] = fmaf(pv[k].re, v[k].im, fmaf(-pv[k].im, v[k].re, d[1]));   // Im (p, res)
+                    d[2] = fmaf(pv[k].re, pv[k].re, fmaf(pv[k].im, pv[k].im, d[2]));  // (p, p)
+                }
             }
         }
-        sap_sum3(d, red);
-        const float ar = d[2] > 0.0f ? d[0] / d[2] : 0.0f, ai = d[2] > 0.0f ? d[1] / d[2] : 0.0f;
-        if (on) {
-            ld_sm(smE, i, v);
-            ld_sm(smX, i, w);
+        if (p == 0 && ph > 1) {   // the MR update after an even half-step
+            sap_sum3(d, red);
+            const float ar = d[2] > 0.0f ? d[0] / d[2] : 0.0f, ai = d[2] > 0.0f ? d[1] / d[2] : 0.0f;
+            if (on) {
+                cx<float> v[12], e[12];
+                ld_sm(smE, i, v);
+                ld_sm(smX, i, e);
 #pragma unroll
-            for (int k = 0; k < 12; k++) {
-                w[k] = w[k] + cx<float>{ar * v[k].re - ai * v[k].im, ar * v[k].im + ai * v[k].re};
-                v[k] = v[k] - cx<float>{ar * pv[k].re - ai * pv[k].im, ar * pv[k].im + ai * pv[k].re};
+                for (int k = 0; k < 12; k++) {
+                    e[k] = e[k] + cx<float>{ar * v[k].re - ai * v[k].im, ar * v[k].im + ai * v[k].re};
+                    v[k] = v[k] - cx<float>{ar * pv[k].re - ai * pv[k].im, ar * pv[k].im + ai * pv[k].re};
+                }
+                st_sm(smE, i, v);
+                st_sm(smX, i, e);
             }
-            st_sm(smE, i, v);
-            st_sm(smX, i, w);
         }
         __syncthreads();
-    }
-
-    // e_o = D_oo^{-1} (r_o - D_oe e_e) = D_oo^{-1} (r_o + 1/2 H_oe e_e); x += e
-    if (on) {
-        sap_hop(a, smX, lo, Go, 1, cbo, w);
-        load_spinor(a.r[1], st, cbo, v);
-#pragma unroll
-        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
-        clover_apply<float>(a.Ci, st, cbo, v, w);
-        load_spinor_rw(a.x[1], st, cbo, v);
-#pragma unroll
-        for (int k = 0; k < 12; k++) v[k] = v[k] + w[k];
-        store_spinor(a.x[1], st, cbo, v);
-        ld_sm(smX, i, w);
-        load_spinor_rw(a.x[0], st, cbe, v);
-#pragma unroll
-        for (int k = 0; k < 12; k++) v[k] = v[k] + w[k];
-        store_spinor(a.x[0], st, cbe, v);
     }
 }
 
