@@ -523,7 +523,6 @@ void sap_apply(lq_ctx *c, const lq_solver_params *p, const void *be, const void 
     Exec e = c->ex();
     zero(e, P32, xe);
     zero(e, P32, xo);
-    void *re = field(c, P32, "sap:re"), *ro = field(c, P32, "sap:ro");
     SapLaunch L;
     std::copy(b, b + 4, L.b);
     L.U[0] = c->U32[0];
@@ -532,19 +531,25 @@ void sap_apply(lq_ctx *c, const lq_solver_params *p, const void *be, const void 
     L.Ci = c->Ci32;
     L.x[0] = xe;
     L.x[1] = xo;
+    // the blocks' even residual and each colour's last correction, on the
+    // sites of that colour's blocks
+    void *res_e = field(c, P32, "sap:re");
+    void *corr[2] = {field(c, P32, "sap:e0"), field(c, P32, "sap:e1")};
+    L.rout_e = res_e;
+    L.eout[0] = corr[0];
+    L.eout[1] = corr[1];
+    L.ro = field(c, P32, "sap:ro");
     L.m = p->smooth_m;
     for (int i = 0; i < p->smooth_n; i++)
         for (int col = 0; col < 2; col++) {
-            if (i == 0 && col == 0) {      // x = 0: r = b
-                L.r[0] = be;
-                L.r[1] = bo;
-            } else {                       // r = b - D x
-                op_full(c, P32, xe, xo, re, ro);
-                axpby(e, P32, 1.0, 0.0, be, -1.0, 0.0, re);
-                axpby(e, P32, 1.0, 0.0, bo, -1.0, 0.0, ro);
-                L.r[0] = re;
-                L.r[1] = ro;
-            }
+            // a colour's first sweep starts from r = b on its blocks (x is zero
+            // there); later sweeps from the residual its last sweep left
+            L.rin[0] = i == 0 ? be : res_e;
+            L.rin[1] = i == 0 ? bo : nullptr;
+            // no correction of the other colour exists before the first launch
+            const bool first = i == 0 && col == 0;
+            L.eface[0] = first ? nullptr : corr[0];
+            L.eface[1] = first ? nullptr : corr[1];
             L.origin = c->sap_origin[col];
             L.count = c->sap_count[col];
             sap_blocks(e, L);

@@ -127,8 +127,12 @@ struct SapLaunch {
     const void *U[2];         // FP32 links by parity
     const void *Ce;           // FP32 C of the even sites
     const void *Ci;           // FP32 C^{-1} of the odd sites
-    const void *r[2];         // FP32 residual by parity
-    void *x[2];               // FP32 solution by parity (updated)
+    const void *rin[2];       // FP32 residual of the blocks before the face update (rin[1] null: zero)
+    const void *eface[2];     // FP32 last correction of the other colour (null: none yet)
+    void *rout_e;             // FP32 out: the blocks' even residual after the solve
+    void *eout[2];            // FP32 out: the blocks' correction
+    void *x[2];               // FP32 solution by parity (x += e)
+    void *ro;                 // FP32 scratch field for the odd residual
     int m;
 };
 void sap_blocks(const Exec &e, const SapLaunch &s);

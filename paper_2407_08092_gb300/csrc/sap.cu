@@ -11,8 +11,20 @@
 // dot products are CTA-local reductions, so an MR step needs no grid-wide
 // synchronisation.  The block's MR residual and iterate and the odd
 // intermediate live in shared memory, where the hops read their neighbours;
-// links and clover blocks come from the global FP32 copies (L1/L2 after the
-// first sweep).
+// links and clover blocks come from the global FP32 copies.
+//
+// The residual r = b - D x each block solve starts from is kept up to date
+// block by block instead of by applying D to the whole lattice before every
+// launch.  After a block's solve its residual is known: the even sites carry
+// the MR residual of the Schur system (r_e - D_ee e_e - D_eo e_o equals
+// r_hat_e - S e_e when e_o is reconstructed as above) and the odd sites none.
+// The blocks adjacent across a face are of the other colour (an even number of
+// blocks along each direction, or one block spanning it), so between two
+// sweeps of a colour x changes only by the other colour's correction e', and
+// the block's residual changes only through the hops that cross its faces:
+//   r_B <- r_B + 1/2 sum over out-of-block neighbours of (1 -+ g_mu) W e'.
+// Each launch stores its blocks' even residual and its correction e; the next
+// launch of the other colour adds the face hops of e in a prologue.
 #include "lq_kernels.h"
 #include "spin.cuh"
 
@@ -28,8 +40,12 @@ struct SapArgs {
     const float4 *U[2];       // FP32 links by parity
     const float4 *Ce;         // C of the even sites
     const float4 *Ci;         // C^{-1} of the odd sites
-    const float4 *r[2];       // residual by parity
-    float4 *x[2];             // solution by parity (updated)
+    const float4 *rin[2];     // the blocks' residual before the face update, by parity (rin[1] null: zero)
+    const float4 *eface[2];   // the other colour's last correction by parity (null: none yet)
+    float4 *rout_e;           // out: the blocks' even residual after the solve
+    float4 *eout[2];          // out: the blocks' correction e by parity
+    float4 *x[2];             // solution by parity (x += e)
+    float4 *ro;               // scratch: the odd residual between the prologue and the last half-step
     int m;                    // Minimal Residual steps
 };
 
@@ -112,6 +128,59 @@ __device__ __forceinline__ void sap_hop(const SapArgs &a, const float2 *src, con
     sap_hop_dir<3>(a, src, l, G, p, cb, acc);
 }
 
+// The hops across the two faces of the block normal to MU: for every site on
+// a face, 1/2 (1 -+ g_mu) W e' of its neighbour outside the block is added to
+// the site's residual in shared memory (smE even, smO odd).  The work items
+// are the face sites, one per thread, so no lane idles on a direction its
+// site does not need; a site lies on at most one of the two faces, so the
+// items of one call touch distinct sites.
+template <int MU>
+__device__ __forceinline__ void sap_face(const SapArgs &a, const int O[4], float2 *smE, float2 *smO)
+{
+    const int ext = a.b[MU], L = a.g.L[MU];
+    if (ext == L) return;              // the block spans the direction: no face
+    const int nf = 2 * a.bvh / ext;    // sites on one face
+    for (int w = threadIdx.x; w < 2 * nf; w += SAP_THREADS) {
+        const int side = w >= nf;      // 0: the face at l_mu = ext - 1 (hop to +mu), 1: at l_mu = 0
+        int f = w - side * nf;
+        int l[4];
+#pragma unroll
+        for (int nu = 0; nu < 4; nu++) {
+            if (nu == MU) {
+                l[nu] = side ? 0 : ext - 1;
+            } else {
+                l[nu] = f % a.b[nu];
+                f /= a.b[nu];
+            }
+        }
+        const int G[4] = {O[0] + l[0], O[1] + l[1], O[2] + l[2], O[3] + l[3]};
+        const int p = (l[0] + l[1] + l[2] + l[3]) & 1;   // block origins have even coordinates
+        int Gn[4] = {G[0], G[1], G[2], G[3]};
+        Gn[MU] = side ? (G[MU] == 0 ? L - 1 : G[MU] - 1) : (G[MU] + 1 == L ? 0 : G[MU] + 1);
+        const long long ncb = sap_global_cb(a.g, Gn);
+        cx<float> psi[12], m[9], acc[12];
+        load_spinor(a.eface[1 - p], a.g.stride, ncb, psi);
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = {0.0f, 0.0f};
+        if (!side) {
+            load_link(a.U[p], a.g.stride, MU, sap_global_cb(a.g, G), m);
+            hop_apply<MU, -1>(acc, psi, m, (MU == 3 && G[3] + 1 == L) ? (float)a.g.tbc : 1.0f);
+        } else {
+            load_link(a.U[1 - p], a.g.stride, MU, ncb, m);
+            hop_apply<MU, +1>(acc, psi, m, (MU == 3 && G[3] == 0) ? (float)a.g.tbc : 1.0f);
+        }
+        float2 *dst = p ? smO : smE;
+        const int ii = (l[0] + a.b[0] * (l[1] + a.b[1] * (l[2] + a.b[2] * l[3]))) >> 1;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            float2 t = dst[c * SAP_THREADS + ii];
+            t.x += 0.5f * acc[c].re;
+            t.y += 0.5f * acc[c].im;
+            dst[c * SAP_THREADS + ii] = t;
+        }
+    }
+}
+
 // sum over the CTA of three floats (all threads receive the totals)
 __device__ __forceinline__ void sap_sum3(float v[3], float *sh)
 {
@@ -133,19 +202,24 @@ __device__ __forceinline__ void sap_sum3(float v[3], float *sh)
     }
 }
 
+#ifndef LQ_SAP_MINB
+#define LQ_SAP_MINB 3
+#endif
+
 // The CTA asks for three resident blocks per SM (at most 168 registers); the
 // MR iterate and residual live in shared memory, not in registers.  The solve
-// is one loop over half-steps, each one block hop into one parity followed by
-// its epilogue, so that a single copy of the hop code serves all of them (the
+// is one loop over half-steps, each one hop into one parity followed by its
+// epilogue, so that a single copy of the hop code serves all of them (the
 // instruction cache holds it):
-//   0      odd:  D_oo^{-1} r_o                               (no hop)
+//   (face) the block's residual rin plus the face hops of e', staged in smE / smO
+//   0      odd:  D_oo^{-1} r_o                               (no hop; r_o kept in ro)
 //   1      even: r_hat = r_e + 1/2 H_eo (D_oo^{-1} r_o); e = 0
-//   2j+2   odd:  t = D_oo^{-1} (-1/2 H_oe res)               (MR step j)
+//   2j+2   odd:  t = D_oo^{-1} (-1/2 H_oe res)                     (MR step j)
 //   2j+3   even: p = C res + 1/2 H_eo t; alpha; e += alpha res; res -= alpha p
-//   2m+2   odd:  e_o = D_oo^{-1} (r_o + 1/2 H_oe e_e); x += e
-__global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
+//   2m+2   odd:  e_o = D_oo^{-1} (r_o + 1/2 H_oe e_e); x += e; store e and res
+__global__ void __launch_bounds__(SAP_THREADS, LQ_SAP_MINB) sap_block_kernel(SapArgs a)
 {
-    __shared__ float2 smE[12 * SAP_THREADS];   // even: r_hat, then the MR residual
+    __shared__ float2 smE[12 * SAP_THREADS];   // even: r_e, r_hat, then the MR residual
     __shared__ float2 smX[12 * SAP_THREADS];   // even: the MR iterate e_e
     __shared__ float2 smO[12 * SAP_THREADS];   // odd: D_oo^{-1} r_o, then t_o
     __shared__ float red[3 * (SAP_THREADS / 32)];
@@ -160,6 +234,33 @@ __global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
     }
     const long long st = a.g.stride;
     const int last = 2 * a.m + 2;
+    const bool face = a.eface[0] != nullptr;
+    if (face) {
+        if (on) {
+            int G[4];
+            cx<float> v[12];
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) G[mu] = O[mu] + le[mu];
+            load_spinor_rw(a.rin[0], st, sap_global_cb(a.g, G), v);
+            st_sm(smE, i, v);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) G[mu] = O[mu] + lo[mu];
+            if (a.rin[1]) load_spinor_rw(a.rin[1], st, sap_global_cb(a.g, G), v);
+            else
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = {0.0f, 0.0f};
+            st_sm(smO, i, v);
+        }
+        __syncthreads();
+        sap_face<0>(a, O, smE, smO);
+        __syncthreads();
+        sap_face<1>(a, O, smE, smO);
+        __syncthreads();
+        sap_face<2>(a, O, smE, smO);
+        __syncthreads();
+        sap_face<3>(a, O, smE, smO);
+        __syncthreads();
+    }
 #pragma unroll 1
     for (int ph = 0; ph <= last; ph++) {
         const int p = (ph == 1 || (ph > 1 && ph < last && (ph & 1))) ? 0 : 1;   // output parity
@@ -176,21 +277,25 @@ __global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
         cx<float> pv[12];
         if (on) {
             cx<float> v[12];
+            if (ph == 0) {   // r_o, kept for the last half-step
+                if (face) ld_sm(smO, i, v);
+                else load_spinor_rw(a.rin[1], st, cb, v);
+                store_spinor(a.ro, st, cb, v);
+            }
             if (p == 1) {   // odd output: D_oo^{-1} (...)
-                if (ph == 0 || ph == last) {
-                    load_spinor(a.r[1], st, cb, v);
-                    if (ph == last) {
+                if (ph == last) {
+                    load_spinor_rw(a.ro, st, cb, v);
 #pragma unroll
-                        for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
-                    }
-                } else {
+                    for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
+                } else if (ph > 0) {
 #pragma unroll
                     for (int k = 0; k < 12; k++) v[k] = -0.5f * w[k];
                 }
                 clover_apply<float>(a.Ci, st, cb, v, pv);
                 if (ph < last) {
                     st_sm(smO, i, pv);
-                } else {   // x += e on both parities of the site pair
+                } else {   // x += e on both parities of the site pair; store e and the residual
+                    store_spinor(a.eout[1], st, cb, pv);
                     load_spinor_rw(a.x[1], st, cb, v);
 #pragma unroll
                     for (int k = 0; k < 12; k++) v[k] = v[k] + pv[k];
@@ -199,21 +304,25 @@ __global__ void __launch_bounds__(SAP_THREADS, 3) sap_block_kernel(SapArgs a)
 #pragma unroll
                     for (int mu = 0; mu < 4; mu++) Ge[mu] = O[mu] + le[mu];
                     const long long cbe = sap_global_cb(a.g, Ge);
+                    ld_sm(smE, i, v);
+                    store_spinor(a.rout_e, st, cbe, v);
                     ld_sm(smX, i, pv);
+                    store_spinor(a.eout[0], st, cbe, pv);
                     load_spinor_rw(a.x[0], st, cbe, v);
 #pragma unroll
                     for (int k = 0; k < 12; k++) v[k] = v[k] + pv[k];
                     store_spinor(a.x[0], st, cbe, v);
                 }
             } else if (ph == 1) {   // r_hat = r_e + 1/2 H_eo (D_oo^{-1} r_o), e = 0
-                load_spinor(a.r[0], st, cb, v);
+                if (face) ld_sm(smE, i, v);   // r_e from the prologue
+                else load_spinor_rw(a.rin[0], st, cb, v);
 #pragma unroll
                 for (int k = 0; k < 12; k++) v[k] = v[k] + 0.5f * w[k];
                 st_sm(smE, i, v);
 #pragma unroll
                 for (int k = 0; k < 12; k++) v[k] = {0.0f, 0.0f};
                 st_sm(smX, i, v);
-            } else {   // p = C res + 1/2 H_eo t and the dot products
+            } else if (ph > 1) {   // p = C res + 1/2 H_eo t and the dot products
                 ld_sm(smE, i, v);
                 clover_apply<float>(a.Ce, st, cb, v, pv);
 #pragma unroll
@@ -253,20 +362,26 @@ void sap_blocks(const Exec &e, const SapLaunch &s)
     for (int mu = 0; mu < 4; mu++) a.b[mu] = s.b[mu];
     a.bvh = s.b[0] * s.b[1] * s.b[2] * s.b[3] / 2;
     a.origin = s.origin;
-    a.U[0] = (const float4 *)s.U[0];
-    a.U[1] = (const float4 *)s.U[1];
+    for (int q = 0; q < 2; q++) {
+        a.U[q] = (const float4 *)s.U[q];
+        a.rin[q] = (const float4 *)s.rin[q];
+        a.eface[q] = (const float4 *)s.eface[q];
+        a.eout[q] = (float4 *)s.eout[q];
+        a.x[q] = (float4 *)s.x[q];
+    }
     a.Ce = (const float4 *)s.Ce;
     a.Ci = (const float4 *)s.Ci;
-    a.r[0] = (const float4 *)s.r[0];
-    a.r[1] = (const float4 *)s.r[1];
-    a.x[0] = (float4 *)s.x[0];
-    a.x[1] = (float4 *)s.x[1];
+    a.rout_e = (float4 *)s.rout_e;
+    a.ro = (float4 *)s.ro;
     a.m = s.m;
-    // per block site and parity: the residual in, links and clover once per
-    // hop sweep from L1/L2, x read and written; per MR step two block hops
+    // per block site pair: the stored residual in, links and clover once per
+    // hop sweep from L1/L2, x read and written, e and the even residual
+    // written; per MR step two block hops, plus the face hops (about a quarter
+    // of a hop per site on 4^4 blocks, counted as such for the flops)
     const double sites = (double)s.count * a.bvh;
-    Launch L_(e, K_SAP, sites * (2 * 96 + 2 * 192 + 8 * 48 + 2 * 288),
-              sites * ((2 * s.m + 2) * (1320 + 552) / 1.0 + s.m * 100));
+    const bool face = s.eface[0] != nullptr;
+    Launch L_(e, K_SAP, sites * (2 * 96 + 2 * 192 + 3 * 96 + 8 * 48 + 2 * 288 + (face ? 2 * 96 : 0)),
+              sites * ((2 * s.m + 2 + (face ? 0.5 : 0.0)) * (1320 + 552) + s.m * 100));
     sap_block_kernel<<<s.count, SAP_THREADS, 0, e.st>>>(a);
 }
 

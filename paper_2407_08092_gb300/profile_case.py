@@ -68,8 +68,21 @@ def main():
         e = torch.empty_like(r)
         prm = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_SAP, smooth_n=3, smooth_m=4, inner_prec=lqdd.LQ_F32,
                                prec=lqdd.LQ_DF64)
+        lqdd.lq_smooth(ctx, prm, r, e)
+        lqdd.lq_profile(ctx, 1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
         for _ in range(a.apps):
             lqdd.lq_smooth(ctx, prm, r, e)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("SAP(3,4)", round(ev[0].elapsed_time(ev[1]) / a.apps, 3), "ms per call")
+        for c in range(lqdd.LQ_K_COUNT):
+            nl, ms, by, fl = lqdd.lq_profile_read(ctx, c)
+            if nl:
+                print(f"{lqdd.lq_kernel_class_name(c):14s} {nl:5d} launches {1e3 * ms / nl:9.2f} us/launch "
+                      f"{by / (ms * 1e6):8.1f} GB/s")
+        lqdd.lq_profile(ctx, 0)
         out = float(e.abs().sum())
     elif a.mode == "force":
         X = torch.from_numpy(synth.gaussian_spinor(V, 71)).cuda()
