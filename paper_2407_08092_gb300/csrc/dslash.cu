@@ -340,25 +340,29 @@ __global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
 // (the same identities as `project` / `reconstruct` above, with s = -1 for the
 // forward and +1 for the backward hop), and the backward link enters as U^+.
 // ---------------------------------------------------------------------------
-// y = C x for both 6x6 blocks, one shared loop body (register arrays are
-// selected, never indexed by the loop variable)
-__device__ __forceinline__ void clover_apply_df(const df2 *__restrict__ C, long long stride, long long s,
-                                                const cx<df64> x[12], cx<df64> y[12])
+// y += A x for one packed Hermitian 6x6 block A (reals 0..5 the diagonal,
+// then the strictly lower entries), read one entry at a time as the product
+// needs it; the six sums are lazily normalised (dl_*) and left unnormalised.
+__device__ __forceinline__ void herm6_fma_df(const df2 *__restrict__ Cb, long long stride, const cx<df64> x[6],
+                                             cx<df64> y[6])
 {
-#pragma unroll 1
-    for (int blk = 0; blk < 2; blk++) {
-        cx<df64> xi[6], yo[6];
 #pragma unroll
-        for (int i = 0; i < 6; i++) xi[i] = blk ? x[6 + i] : x[i];
-        df64 a[36];
-        load_block(C, stride, blk, s, a);
-        herm6_apply<df64>(a, xi, yo);
-#pragma unroll
-        for (int i = 0; i < 6; i++) {
-            if (blk) y[6 + i] = yo[i];
-            else y[i] = yo[i];
-        }
+    for (int k = 0; k < 3; k++) {   // the diagonal: reals 2k, 2k+1
+        const df2 t = ldg(Cb + k * stride);
+        const df64 d0(t.rh, t.rl), d1(t.ih, t.il);
+        dl_fma(y[2 * k].re, d0, x[2 * k].re);
+        dl_fma(y[2 * k].im, d0, x[2 * k].im);
+        dl_fma(y[2 * k + 1].re, d1, x[2 * k + 1].re);
+        dl_fma(y[2 * k + 1].im, d1, x[2 * k + 1].im);
     }
+#pragma unroll
+    for (int i = 1; i < 6; i++)
+#pragma unroll
+        for (int j = 0; j < i; j++) {
+            const cx<df64> l = df2_cx(ldg(Cb + (3 + tri(i, j)) * stride));
+            dl_cfma(y[i], l, x[j]);    // lower entry
+            dl_cfmac(y[j], l, x[i]);   // its conjugate above the diagonal
+        }
 }
 
 __device__ __forceinline__ cx<df64> rot_i(cx<df64> z, int q)   // i^q z
@@ -375,7 +379,10 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
     // and psi_2 for z, t (acc_2 takes u_1 resp. u_0); the i-powers
     //   qa = {1,3,0,2,1,3,2,0}, qb = {1,3,2,0,3,1,2,0},
     //   qc = {3,1,2,0,3,1,2,0}, qd = {3,1,0,2,1,3,2,0}
-    // are packed two bits per direction (no local-memory tables)
+    // are packed two bits per direction (no local-memory tables).  The
+    // neighbour's components and the link's entries are read as the
+    // projection and the product use them, and every sum is lazily normalised
+    // (dl_*): acc is renormalised once, after the eight directions.
     constexpr unsigned QA = 11661u, QB = 10029u, QC = 10023u, QD = 11655u;
     const long long st = g.stride;
     cx<df64> acc[12];
@@ -400,83 +407,109 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
             else nb = (coord == 0) ? s + (long long)(ext - 1) * dd : s - dd;
             if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
         }
-        cx<df64> p[12];
-        load_spinor(in, st, nb, p);
-        cx<df64> m[9];
-        load_link(fwd ? k.Uout : k.Uin, st, mu, fwd ? s : nb, m);
+        const df2 *pn = in + nb;
         const int pa = d < 4 ? 3 : 2;
         const int qa = (QA >> (2 * d)) & 3, qb = (QB >> (2 * d)) & 3;
         cx<df64> h[6];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const cx<df64> q0 = pa == 3 ? p[9 + a] : p[6 + a];
-            const cx<df64> q1 = pa == 3 ? p[6 + a] : p[9 + a];
-            h[a] = p[a] + rot_i(q0, qa);
-            h[3 + a] = p[3 + a] + rot_i(q1, qb);
+            h[a] = df2_cx(ldg(pn + a * st));
+            dl_cadd(h[a], rot_i(df2_cx(ldg(pn + (pa == 3 ? 9 + a : 6 + a) * st)), qa));
+            h[3 + a] = df2_cx(ldg(pn + (3 + a) * st));
+            dl_cadd(h[3 + a], rot_i(df2_cx(ldg(pn + (pa == 3 ? 6 + a : 9 + a) * st)), qb));
         }
-        cx<df64> u[6];
-#pragma unroll
-        for (int hs = 0; hs < 2; hs++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                // row a of U (forward) or of U^+ (backward): entries m[a*3+b] or conj(m[b*3+a])
-                cx<df64> e0 = fwd ? m[a * 3 + 0] : cconj(m[0 * 3 + a]);
-                cx<df64> e1 = fwd ? m[a * 3 + 1] : cconj(m[1 * 3 + a]);
-                cx<df64> e2 = fwd ? m[a * 3 + 2] : cconj(m[2 * 3 + a]);
-                cx<df64> t = cmul(e0, h[hs * 3 + 0]);
-                t = cfma(e1, h[hs * 3 + 1], t);
-                t = cfma(e2, h[hs * 3 + 2], t);
-                u[hs * 3 + a] = flip ? -t : t;
-            }
+        const df2 *Um = (fwd ? k.Uout : k.Uin) + (long long)mu * 9 * st + (fwd ? s : nb);
         const int ra = d < 4 ? 1 : 0;
         const int qc = (QC >> (2 * d)) & 3, qd = (QD >> (2 * d)) & 3;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            acc[a] = acc[a] + u[a];
-            acc[3 + a] = acc[3 + a] + u[3 + a];
-            const cx<df64> v2 = ra ? u[3 + a] : u[a];
-            const cx<df64> v3 = ra ? u[a] : u[3 + a];
-            acc[6 + a] = acc[6 + a] + rot_i(v2, qc);
-            acc[9 + a] = acc[9 + a] + rot_i(v3, qd);
+            // row a of U (forward) or of U^+ (backward): entries m[a*3+b] or conj(m[b*3+a])
+            cx<df64> e[3];
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                const cx<df64> t = df2_cx(ldg(Um + (fwd ? a * 3 + b : b * 3 + a) * st));
+                e[b] = fwd ? t : cx<df64>{t.re, dl_neg(t.im)};
+            }
+            cx<df64> u0 = dl_cmul(e[0], h[0]), u1 = dl_cmul(e[0], h[3]);
+            dl_cfma(u0, e[1], h[1]);
+            dl_cfma(u1, e[1], h[4]);
+            dl_cfma(u0, e[2], h[2]);
+            dl_cfma(u1, e[2], h[5]);
+            if (flip) {
+                u0 = {dl_neg(u0.re), dl_neg(u0.im)};
+                u1 = {dl_neg(u1.re), dl_neg(u1.im)};
+            }
+            dl_cadd(acc[a], u0);
+            dl_cadd(acc[3 + a], u1);
+            dl_cadd(acc[6 + a], rot_i(ra ? u1 : u0, qc));
+            dl_cadd(acc[9 + a], rot_i(ra ? u0 : u1, qd));
         }
     }
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc[i] = dl_cnorm(acc[i]);
 
-    cx<df64> v[12];
-    const df64 half(0.5f, 0.0f), mhalf(-0.5f, 0.0f);
-    if (MODE == HOP_K1) {
+    // the site term, one 6x6 clover block (spins 0,1 then 2,3) at a time: six
+    // components of the output are formed and stored per block (register
+    // arrays are selected by the block, never indexed by it)
+#pragma unroll 1
+    for (int blk = 0; blk < 2; blk++) {
+        const long long o = (long long)blk * 6 * st + s;
+        const df2 *Cb = k.clov + (long long)blk * 18 * st + s;
+        cx<df64> a6[6], y[6];
 #pragma unroll
-        for (int i = 0; i < 12; i++) acc[i] = mhalf * acc[i];
-        clover_apply_df(k.clov, st, s, acc, v);
-    } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
-        cx<df64> x[12];
-        load_spinor_rw(in2, st, s, x);
-        clover_apply_df(k.clov, st, s, x, v);
-        const df64 f = MODE == HOP_FULL ? mhalf : half;
+        for (int i = 0; i < 6; i++) a6[i] = blk ? acc[6 + i] : acc[i];
+        if (MODE == HOP_K1) {   // y = C (-1/2 acc)
 #pragma unroll
-        for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
-        if (MODE == HOP_RICH) {
-            cx<df64> bb[12];
-            load_spinor(bv, st, s, bb);
+            for (int i = 0; i < 6; i++) {
+                a6[i] = {dl_scale2(a6[i].re, -0.5f), dl_scale2(a6[i].im, -0.5f)};
+                y[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+            }
+            herm6_fma_df(Cb, st, a6, y);
 #pragma unroll
-            for (int i = 0; i < 12; i++) v[i] = x[i] + k.omega * (bb[i] - v[i]);
+            for (int i = 0; i < 6; i++) y[i] = dl_cnorm(y[i]);
+        } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {   // y = C x +- 1/2 acc
+            const float f = MODE == HOP_FULL ? -0.5f : 0.5f;
+            cx<df64> x6[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                x6[i] = df2_cx(in2[o + i * st]);
+                y[i] = {dl_scale2(a6[i].re, f), dl_scale2(a6[i].im, f)};
+            }
+            herm6_fma_df(Cb, st, x6, y);
+#pragma unroll
+            for (int i = 0; i < 6; i++) y[i] = dl_cnorm(y[i]);
+            if (MODE == HOP_RICH) {   // x + omega (b - D x)
+#pragma unroll
+                for (int i = 0; i < 6; i++) y[i] = x6[i] + k.omega * (df2_cx(ldg(bv + o + i * st)) - y[i]);
+            }
+        } else {   // y = in2 + 1/2 acc, and for the reconstruction C^{-1} of that
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                cx<df64> t = df2_cx(in2[o + i * st]);
+                dl_cadd(t, {dl_scale2(a6[i].re, 0.5f), dl_scale2(a6[i].im, 0.5f)});
+                a6[i] = dl_cnorm(t);
+            }
+            if (MODE == HOP_RECON) {
+#pragma unroll
+                for (int i = 0; i < 6; i++) y[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+                herm6_fma_df(Cb, st, a6, y);
+#pragma unroll
+                for (int i = 0; i < 6; i++) y[i] = dl_cnorm(y[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; i++) y[i] = a6[i];
+            }
         }
-    } else {
-        cx<df64> y[12];
-        load_spinor_rw(in2, st, s, y);
 #pragma unroll
-        for (int i = 0; i < 12; i++) y[i] = y[i] + half * acc[i];
-        if (MODE == HOP_RECON) {
-            clover_apply_df(k.clov, st, s, y, v);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 12; i++) v[i] = y[i];
-        }
+        for (int i = 0; i < 6; i++) out[o + i * st] = cx_df2(y[i]);
     }
-    store_spinor(out, st, s, v);
 }
 
+#ifndef LQ_DF_MINB
+#define LQ_DF_MINB 1
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(128) hop_df_kernel(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(128, LQ_DF_MINB) hop_df_kernel(const __grid_constant__ Geom g,
                                                      const __grid_constant__ HopArgs<df64> k)
 {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
