@@ -85,25 +85,13 @@ __global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const df2 *__
                     for (int b = 0; b < 3; b++) d.a[a * 3 + b] = cconj(Lk.a[b * 3 + a]);
                 Lk = d;
             }
-            if (i == 0) {
-                T = Lk;
-            } else {
-                M3<df64> P;
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-#pragma unroll
-                    for (int b = 0; b < 3; b++) {
-                        cx<df64> acc = cmul(T.a[a * 3], Lk.a[b]);
-                        acc = cfma(T.a[a * 3 + 1], Lk.a[3 + b], acc);
-                        acc = cfma(T.a[a * 3 + 2], Lk.a[6 + b], acc);
-                        P.a[a * 3 + b] = acc;
-                    }
-                T = P;
-            }
+            T = i == 0 ? Lk : mat_mul(T, Lk);
         }
 #pragma unroll
-        for (int k = 0; k < 9; k++) Q.a[k] = Q.a[k] + T.a[k];
+        for (int k = 0; k < 9; k++) dl_cadd(Q.a[k], T.a[k]);   // renormalised after the four leaves
     }
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q.a[k] = dl_cnorm(Q.a[k]);
     // F = (Q - Q^+)/8: Im F_aa, then F_01, F_02, F_12
     const df64 eighth(0.125f, 0.0f);
     auto fa = [&](int a, int b) { return eighth * (Q.a[a * 3 + b] - cconj(Q.a[b * 3 + a])); };

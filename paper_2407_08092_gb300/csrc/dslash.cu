@@ -389,24 +389,31 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
 #pragma unroll
     for (int i = 0; i < 12; i++) acc[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
 
+    // the neighbour's checkerboard index in direction d, and whether the time
+    // boundary flips the sign of the hop
+    auto neighbour = [&](int d, bool &flip) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        flip = false;
+        if (mu == 0) {
+            const int xn = fwd ? (c.x + 1 == g.L[0] ? 0 : c.x + 1) : (c.x == 0 ? g.L[0] - 1 : c.x - 1);
+            return c.row * g.Lxh + (xn >> 1);
+        }
+        const int coord = mu == 1 ? c.y : mu == 2 ? c.z : c.t;
+        const int ext = g.L[mu];
+        const long long dd = mu == 1 ? (long long)g.Lxh
+                           : mu == 2 ? (long long)g.Lxh * g.L[1] : (long long)g.Lxh * g.L[1] * g.L[2];
+        if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
+        if (fwd) return (coord + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd;
+        return (coord == 0) ? s + (long long)(ext - 1) * dd : s - dd;
+    };
+
 #pragma unroll 1
     for (int d = 0; d < 8; d++) {
         const int mu = d >> 1;
         const bool fwd = (d & 1) == 0;
-        long long nb;
-        bool flip = false;
-        if (mu == 0) {
-            const int xn = fwd ? (c.x + 1 == g.L[0] ? 0 : c.x + 1) : (c.x == 0 ? g.L[0] - 1 : c.x - 1);
-            nb = c.row * g.Lxh + (xn >> 1);
-        } else {
-            const int coord = mu == 1 ? c.y : mu == 2 ? c.z : c.t;
-            const int ext = g.L[mu];
-            const long long dd = mu == 1 ? (long long)g.Lxh
-                               : mu == 2 ? (long long)g.Lxh * g.L[1] : (long long)g.Lxh * g.L[1] * g.L[2];
-            if (fwd) nb = (coord + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd;
-            else nb = (coord == 0) ? s + (long long)(ext - 1) * dd : s - dd;
-            if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
-        }
+        bool flip;
+        const long long nb = neighbour(d, flip);
         const df2 *pn = in + nb;
         const int pa = d < 4 ? 3 : 2;
         const int qa = (QA >> (2 * d)) & 3, qb = (QB >> (2 * d)) & 3;

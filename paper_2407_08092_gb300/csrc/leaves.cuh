@@ -83,6 +83,24 @@ __device__ __forceinline__ M3<R> mat_mul(const M3<R> &A, const M3<R> &B)
     return P;
 }
 
+// df64: each entry is a lazily normalised compensated sum of its three
+// complex products (dl_*), renormalised once
+template <>
+__device__ __forceinline__ M3<df64> mat_mul<df64>(const M3<df64> &A, const M3<df64> &B)
+{
+    M3<df64> P;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            cx<df64> acc = dl_cmul(A.a[a * 3], B.a[b]);
+            dl_cfma(acc, A.a[a * 3 + 1], B.a[3 + b]);
+            dl_cfma(acc, A.a[a * 3 + 2], B.a[6 + b]);
+            P.a[a * 3 + b] = dl_cnorm(acc);
+        }
+    return P;
+}
+
 // An anti-Hermitian 3x3 matrix A is stored as 9 reals, as df64 pairs in
 // [plane][9][V] float2: Im A_aa (a = 0, 1, 2), then A_01, A_02, A_12 (re, im).
 __device__ __forceinline__ M3<df64> load_antiherm(const float2 *__restrict__ base, long long V, long long lex, int p)
