@@ -124,7 +124,9 @@ typedef struct {
 } lq_stats;
 
 /* Create a context for one lattice on the current CUDA device.  `stream` is a
- * cudaStream_t (NULL: the legacy default stream).  *out receives the context. */
+ * cudaStream_t (NULL: the legacy default stream).  *out receives the context.
+ * LQ_ERR_ARG for an odd or < 2 extent, t_bc not +-1, non-finite m0 / c_sw, or
+ * a volume of 2^31 sites or more (one FP64 spinor field would exceed HBM). */
 lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream);
 
 /* Release the context and all library-owned device and host memory. */

@@ -44,6 +44,8 @@ struct lq_ctx {
     Counters ctr;
     int device;
     bool have_gauge = false;
+    bool clover64 = false;            // C64 / Ci64 rounded from the current df64 blocks
+    bool links16 = false;             // U16 rounded from the current FP32 links
     void *U64[2] = {nullptr, nullptr};
     void *U32[2] = {nullptr, nullptr};
     void *C64[2] = {nullptr, nullptr};
@@ -174,13 +176,34 @@ void need_gauge(lq_ctx *c)
     if (!c->have_gauge) fail(c, LQ_ERR_STATE, "no gauge field: call lq_set_gauge first");
 }
 
+// The FP64 clover blocks and the BF16 links are rounded copies that only the
+// FP64 operator and the BF16 hops read: they are made on first use after each
+// lq_set_gauge, on the context's stream.
+void need_clover64(lq_ctx *c)
+{
+    if (c->clover64) return;
+    Exec e = c->ex();
+    for (int p = 0; p < 2; p++) clover_to_f64(e, c->Cdf[p], c->C64[p]);
+    clover_to_f64(e, c->Cidf, c->Ci64);
+    c->clover64 = true;
+}
+void need_links16(lq_ctx *c)
+{
+    if (c->links16) return;
+    Exec e = c->ex();
+    for (int p = 0; p < 2; p++) links_to_bf16(e, c->U32[p], c->U16[p]);
+    c->links16 = true;
+}
+
 // clover blocks of a precision (BF16 fields use the FP32 blocks)
 const void *Cp(lq_ctx *c, int prec, int parity)
 {
+    if (prec == P64) need_clover64(c);
     return prec == P64 ? c->C64[parity] : (prec == P32 || prec == P16) ? c->C32[parity] : c->Cdf[parity];
 }
 const void *Cip(lq_ctx *c, int prec)
 {
+    if (prec == P64) need_clover64(c);
     return prec == P64 ? c->Ci64 : (prec == P32 || prec == P16) ? c->Ci32 : c->Cidf;
 }
 bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_DF64; }
@@ -191,6 +214,7 @@ HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
     h.mode = mode;
     h.prec = prec;
     h.pout = pout;
+    if (prec == P16) need_links16(c);
     for (int p = 0; p < 2; p++)
         h.U[p] = prec == P64 ? c->U64[p] : prec == P32 ? c->U32[p] : prec == P16 ? c->U16[p] : c->Udf[p];
     return h;
@@ -1208,7 +1232,7 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
     if (lat->t_bc != 1 && lat->t_bc != -1) return LQ_ERR_ARG;
     if (!std::isfinite(lat->m0) || !std::isfinite(lat->csw)) return LQ_ERR_ARG;
     const long long V = (long long)lat->L[0] * lat->L[1] * lat->L[2] * lat->L[3];
-    if (V > (1LL << 40)) return LQ_ERR_ARG;
+    if (V >= (1LL << 31)) return LQ_ERR_ARG;   // one FP64 spinor of 2^31 sites would exceed HBM
     lq_ctx *c = new (std::nothrow) lq_ctx();
     if (!c) return LQ_ERR_OOM;
     c->lat = *lat;
@@ -1272,15 +1296,16 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
             for (int p = 0; p < 2; p++) c->U16[p] = dev_alloc(c, (size_t)4 * 3 * g.stride * 8);
         }
         c->have_gauge = false;
-        // links in every precision; clover and inverse built in df64, their
-        // FP64 and FP32 copies rounded by the same kernels
+        c->clover64 = false;
+        c->links16 = false;
+        // links in FP64, FP32 and df64; clover and inverse built in df64, their
+        // FP32 copies rounded by the same kernels (FP64 clover and BF16 links
+        // follow on first use)
         import_links(e, U, c->U64, c->U32, c->Udf);
-        for (int p = 0; p < 2; p++) links_to_bf16(e, c->U32[p], c->U16[p]);
         const void *udf[2] = {c->Udf[0], c->Udf[1]};
-        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C64, c->C32,
-                     ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
+        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C32, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
-        clover_invert(e, c->Cdf[1], c->Cidf, c->Ci64, c->Ci32, c->dflag);
+        clover_invert(e, c->Cdf[1], c->Cidf, c->Ci32, c->dflag);
         ck_launch(c, "set_gauge kernels");
         int flag = 0;
         ck(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "cudaMemcpyAsync");
@@ -1807,6 +1832,7 @@ lq_status lq_export_clover(lq_ctx *c, int which, void *out)
     return guarded(c, [&] {
         if (!out || (which != 0 && which != 1)) fail(c, LQ_ERR_ARG, "bad argument");
         need_gauge(c);
+        need_clover64(c);
         Exec e = c->ex();
         if (which == 0) clover_export(e, c->C64[0], c->C64[1], out);
         else clover_export(e, nullptr, c->Ci64, out);

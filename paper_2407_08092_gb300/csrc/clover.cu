@@ -14,7 +14,8 @@
 //
 // The library builds and inverts in df64 (FP64-accurate, on the FP32 units,
 // which GB300 runs at 64 times its FP64 rate); the assembly and inverse kernels
-// also write the FP64 and FP32 copies, rounded from df64.  The build is split in two launches: one thread per
+// also write the FP32 copies, rounded from df64.  The FP64 copies are rounded
+// from df64 by clover_to_f64 when an FP64 operator first needs them.  The build is split in two launches: one thread per
 // (site, plane) computes the four leaves and F of that plane into a scratch
 // array, then one thread per site assembles the two 6x6 blocks.
 #include "leaves.cuh"
@@ -25,20 +26,17 @@ namespace lq {
 __device__ __forceinline__ void store_pair(double2 *p, double a, double b) { *p = make_double2(a, b); }
 
 // one packed 6x6 block (36 df64 reals) of the site with checkerboard index s:
-// the df64 copy and its rounding to FP64 and FP32 (FP32: two complex slots per
-// float4)
-__device__ __forceinline__ void store_block_all(const Geom &g, int b, long long s, const df64 r[36], df2 *Cdf,
-                                                double2 *C64, float4 *C32)
+// the df64 copy and its rounding to FP32 (two complex slots per float4)
+__device__ __forceinline__ void store_block_df32(const Geom &g, int b, long long s, const df64 r[36], df2 *Cdf,
+                                                 float4 *C32)
 {
 #pragma unroll
     for (int k = 0; k < 9; k++) {
         const df64 a0 = r[4 * k], a1 = r[4 * k + 1], a2 = r[4 * k + 2], a3 = r[4 * k + 3];
         Cdf[(b * 18 + 2 * k) * g.stride + s] = df2{a0.hi, a0.lo, a1.hi, a1.lo};
         Cdf[(b * 18 + 2 * k + 1) * g.stride + s] = df2{a2.hi, a2.lo, a3.hi, a3.lo};
-        const double d0 = df_to_double(a0), d1 = df_to_double(a1), d2 = df_to_double(a2), d3 = df_to_double(a3);
-        C64[(b * 18 + 2 * k) * g.stride + s] = make_double2(d0, d1);
-        C64[(b * 18 + 2 * k + 1) * g.stride + s] = make_double2(d2, d3);
-        C32[(b * 9 + k) * g.stride + s] = make_float4((float)d0, (float)d1, (float)d2, (float)d3);
+        C32[(b * 9 + k) * g.stride + s] = make_float4((float)df_to_double(a0), (float)df_to_double(a1),
+                                                      (float)df_to_double(a2), (float)df_to_double(a3));
     }
 }
 __device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.hi, a.lo, b.hi, b.lo}; }
@@ -120,8 +118,8 @@ __device__ __forceinline__ cx<df64> f_entry(const float2 *__restrict__ Fb, long 
 // block b: G1 = -F_yz +- F_xt, G2 = F_xz +- F_yt, G3 = -F_xy +- F_zt (+ for b = 0),
 // M = i h [[G3, G1 - i G2], [G1 + i G2, -G3]], h = c_sw / 2, C = (4 + m0) + M.
 __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const float2 *__restrict__ Fb, double csw,
-                                                              double m0, df2 *Ce, df2 *Co, double2 *C64e,
-                                                              double2 *C64o, float4 *C32e, float4 *C32o)
+                                                              double m0, df2 *Ce, df2 *Co, float4 *C32e,
+                                                              float4 *C32o)
 {
     const long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (lex >= g.V) return;
@@ -144,15 +142,16 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
             const cx<df64> s = l == 1 ? fs : -fs;
             return plus ? s + ft : s - ft;
         };
-        df64 out[36];
-#pragma unroll 1
+        df64 out[36];   // every index below is a constant: the block stays in registers
+#pragma unroll
         for (int i = 0; i < 6; i++) {
             const int si = i / 3, ai = i % 3;
             const df64 v = -(h * G(2, ai, ai).im);          // Re(i h G3_aa) = -h Im(G3_aa)
             out[i] = si == 0 ? diag + v : diag - v;
         }
-#pragma unroll 1
+#pragma unroll
         for (int i = 1; i < 6; i++)
+#pragma unroll
             for (int j = 0; j < i; j++) {
                 const int si = i / 3, ai = i % 3, sj = j / 3, aj = j % 3;
                 cx<df64> m;
@@ -166,70 +165,109 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
                 out[k] = m.re;
                 out[k + 1] = m.im;
             }
-        store_block_all(g, b, cb, out, C, parity ? C64o : C64e, parity ? C32o : C32e);
+        store_block_df32(g, b, cb, out, C, parity ? C32o : C32e);
     }
 }
 
-// LDL^+ factorisation and inverse of one packed Hermitian 6x6 block.
-// A = L D L^+ (L unit lower, D real); A^{-1} = L^{-+} D^{-1} L^{-1}.
-template <typename R>
-__global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const typename St<R>::vec *__restrict__ C,
-                                                            typename St<R>::vec *Ci, double2 *Ci64, float4 *Ci32,
-                                                            int *flag)
+// LDL^+ factorisation and inverse of one packed Hermitian 6x6 block in df64:
+// A = L D L^+ (L unit lower, D real), X = L^{-1}, A^{-1} = X^+ D^{-1} X.
+// Every loop is unrolled, so the factors live in registers, and the sums are
+// lazily normalised compensated sums (dl_*).
+__global__ void __launch_bounds__(128) clover_invert_kernel(Geom g, const df2 *__restrict__ C, df2 *Ci,
+                                                            float4 *Ci32, int *flag)
 {
-    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 2 * g.Vh) return;
     const int b = (int)(id / g.Vh);
     const long long s = id - b * g.Vh;
-    R r[36];
+    df64 r[36];
     load_block(C, g.stride, b, s, r);
-    cx<R> Lm[6][6];
-    R D[6];
-    for (int i = 0; i < 6; i++)
-        for (int j = 0; j < 6; j++) Lm[i][j] = {R(i == j ? 1.0 : 0.0), R(0.0)};
+    cx<df64> L[15];   // strictly lower entries, packed by tri(i, j)
+    df64 D[6], Dinv[6];
     bool bad = false;
+#pragma unroll
     for (int j = 0; j < 6; j++) {
-        R d = r[j];
-        for (int k = 0; k < j; k++) d = d - (Lm[j][k].re * Lm[j][k].re + Lm[j][k].im * Lm[j][k].im) * D[k];
-        if (!positive(d)) bad = true;   // Hermitian positive definite expected; NaN fails too
+        // c_k = D_k conj(L_jk), k < j
+        cx<df64> cj[5];
+#pragma unroll
+        for (int k = 0; k < j; k++) {
+            const cx<df64> l = L[tri(j, k)];
+            cj[k] = {D[k] * l.re, dl_neg(D[k] * l.im)};
+        }
+        // D_j = A_jj - sum_k Re(L_jk c_k)
+        df64 d = r[j];
+#pragma unroll
+        for (int k = 0; k < j; k++) {
+            dl_fma(d, dl_neg(L[tri(j, k)].re), cj[k].re);
+            dl_fma(d, L[tri(j, k)].im, cj[k].im);
+        }
+        d = dl_norm(d);
+        if (!df_positive(d)) bad = true;   // Hermitian positive definite expected; NaN fails too
         D[j] = d;
-        const R dinv = R(1.0) / d;
+        Dinv[j] = df64(1.0f, 0.0f) / d;
+        // L_ij = (A_ij - sum_k L_ik c_k) / D_j, i > j
+#pragma unroll
         for (int i = j + 1; i < 6; i++) {
             const int kk = 6 + 2 * tri(i, j);
-            cx<R> a = {r[kk], r[kk + 1]};
-            for (int k = 0; k < j; k++) a = a - D[k] * cmul(Lm[i][k], cconj(Lm[j][k]));
-            Lm[i][j] = dinv * a;
+            cx<df64> a = {r[kk], r[kk + 1]};
+#pragma unroll
+            for (int k = 0; k < j; k++) dl_cfma(a, {dl_neg(L[tri(i, k)].re), dl_neg(L[tri(i, k)].im)}, cj[k]);
+            a = dl_cnorm(a);
+            L[tri(i, j)] = {a.re * Dinv[j], a.im * Dinv[j]};
         }
     }
-    // X = L^{-1} (unit lower) by forward substitution
-    cx<R> X[6][6];
-    for (int i = 0; i < 6; i++)
-        for (int j = 0; j < 6; j++) X[i][j] = {R(i == j ? 1.0 : 0.0), R(0.0)};
+    // X = L^{-1}: X_ij = -(L_ij + sum_{j<k<i} L_ik X_kj), i > j
+    cx<df64> X[15];
+#pragma unroll
     for (int i = 1; i < 6; i++)
+#pragma unroll
         for (int j = 0; j < i; j++) {
-            cx<R> acc = {R(0.0), R(0.0)};
-            for (int k = j; k < i; k++) acc = cfma(Lm[i][k], X[k][j], acc);
-            X[i][j] = -acc;
+            cx<df64> acc = L[tri(i, j)];
+#pragma unroll
+            for (int k = j + 1; k < i; k++) dl_cfma(acc, L[tri(i, k)], X[tri(k, j)]);
+            acc = dl_cnorm(acc);
+            X[tri(i, j)] = {dl_neg(acc.re), dl_neg(acc.im)};
         }
-    R Dinv[6];
-    for (int k = 0; k < 6; k++) Dinv[k] = R(1.0) / D[k];
-    // A^{-1}_{ij} = sum_{k >= max(i,j)} conj(X_ki) X_kj / D_k  (lower part, i >= j)
-    R out[36];
+    // A^{-1}_ij = sum_{k >= i} conj(X_ki) X_kj / D_k (i >= j, X_kk = 1)
+    df64 out[36];
+#pragma unroll
     for (int i = 0; i < 6; i++) {
-        R acc = R(0.0);
-        for (int k = i; k < 6; k++) acc = acc + (X[k][i].re * X[k][i].re + X[k][i].im * X[k][i].im) * Dinv[k];
-        out[i] = acc;
+        df64 acc = Dinv[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; k++) {
+            const cx<df64> x = X[tri(k, i)];
+            const df64 m2 = dl_norm([&] { df64 t = dl_prod(x.re, x.re); dl_fma(t, x.im, x.im); return t; }());
+            dl_fma(acc, m2, Dinv[k]);
+        }
+        out[i] = dl_norm(acc);
     }
+#pragma unroll
     for (int i = 1; i < 6; i++)
+#pragma unroll
         for (int j = 0; j < i; j++) {
-            cx<R> acc = {R(0.0), R(0.0)};
-            for (int k = i; k < 6; k++) acc = acc + Dinv[k] * cmulc(X[k][i], X[k][j]);
+            const cx<df64> xij = X[tri(i, j)];
+            cx<df64> acc = {dl_prod(Dinv[i], xij.re), dl_prod(Dinv[i], xij.im)};
+#pragma unroll
+            for (int k = i + 1; k < 6; k++) {
+                const cx<df64> y = {Dinv[k] * X[tri(k, j)].re, Dinv[k] * X[tri(k, j)].im};
+                dl_cfmac(acc, X[tri(k, i)], y);
+            }
+            acc = dl_cnorm(acc);
             const int kk = 6 + 2 * tri(i, j);
             out[kk] = acc.re;
             out[kk + 1] = acc.im;
         }
-    store_block_all(g, b, s, out, Ci, Ci64, Ci32);
+    store_block_df32(g, b, s, out, Ci, Ci32);
     if (bad) atomicAdd(flag, 1);
+}
+
+// df64 clover blocks (both 6x6 blocks of n sites' fields) rounded to FP64
+__global__ void clover_f64_kernel(long long n, const df2 *__restrict__ in, double2 *out)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df2 t = in[i];
+    out[i] = make_double2((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
 }
 
 __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, const double2 *__restrict__ Co,
@@ -265,8 +303,8 @@ __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, con
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C64[2],
-                  void *C32[2], void *Fscratch)
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C32[2],
+                  void *Fscratch)
 {
     {
         // unique bytes per site: its four df64 links (4 x 144) and the six F
@@ -277,18 +315,24 @@ void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void
                                                                                 (const df2 *)Udf[1],
                                                                                 (float2 *)Fscratch);
     }
-    // reads the six F, writes the blocks in df64, FP64 and FP32
-    Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * (8 + 8 + 4)));
+    // reads the six F, writes the blocks in df64 and FP32
+    Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * (8 + 4)));
     clover_assemble_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(
-        e.g, (const float2 *)Fscratch, csw, m0, (df2 *)Cdf[0], (df2 *)Cdf[1], (double2 *)C64[0],
-        (double2 *)C64[1], (float4 *)C32[0], (float4 *)C32[1]);
+        e.g, (const float2 *)Fscratch, csw, m0, (df2 *)Cdf[0], (df2 *)Cdf[1], (float4 *)C32[0], (float4 *)C32[1]);
 }
 
-void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci64, void *Ci32, int *flag)
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci32, int *flag)
 {
-    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 8 + 8 + 4), (double)e.g.Vh * 2 * 1500);
-    clover_invert_kernel<df64><<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(
-        e.g, (const df2 *)Cdf, (df2 *)Cidf, (double2 *)Ci64, (float4 *)Ci32, flag);
+    Launch L_(e, K_CLOVER, (double)e.g.Vh * 72 * (8 + 8 + 4), (double)e.g.Vh * 2 * 1500);
+    clover_invert_kernel<<<blocks_for(2 * e.g.Vh, 128), 128, 0, e.st>>>(e.g, (const df2 *)Cdf, (df2 *)Cidf,
+                                                                          (float4 *)Ci32, flag);
+}
+
+void clover_to_f64(const Exec &e, const void *Cdf, void *C64)
+{
+    const long long n = 36LL * e.g.stride;   // two blocks of 18 complex slots
+    Launch L_(e, K_LAYOUT, (double)n * 32);
+    clover_f64_kernel<<<blocks_for(n, 256), 256, 0, e.st>>>(n, (const df2 *)Cdf, (double2 *)C64);
 }
 
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out)

@@ -8,185 +8,202 @@ namespace lq {
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// one thread per (site, mu): U_nat[lex][mu][9] -> U64[p][mu][9][stride], U32[p][mu][3][stride]
 __device__ __forceinline__ df2 to_df2(double2 v)
 {
-    const df64 r(v.x), i(v.y);
+    const df64 r = df_split(v.x), i = df_split(v.y);
     return df2{r.hi, r.lo, i.hi, i.lo};
 }
-__device__ __forceinline__ double2 from_df2(df2 v)
+__device__ __forceinline__ double2 from_df2(df2 v) { return make_double2(df_join(v.rh, v.rl), df_join(v.ih, v.il)); }
+
+// parity of lattice site lex (32-bit arithmetic: a lattice of 2^31 sites
+// would not fit one spinor field in HBM, and lq_create rejects it)
+__device__ __forceinline__ int lex_parity(const Geom &g, long long lex)
 {
-    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+    unsigned r = (unsigned)lex;
+    const unsigned c0 = r % (unsigned)g.L[0];
+    r /= (unsigned)g.L[0];
+    const unsigned c1 = r % (unsigned)g.L[1];
+    r /= (unsigned)g.L[1];
+    const unsigned c2 = r % (unsigned)g.L[2], c3 = r / (unsigned)g.L[2];
+    return (int)((c0 + c1 + c2 + c3) & 1u);
 }
 
-__global__ void import_links_kernel(Geom g, const double2 *__restrict__ U, double2 *U64e, double2 *U64o,
-                                    float4 *U32e, float4 *U32o, df2 *Udfe, df2 *Udfo)
+// The natural fields are row-major [site][components] arrays of complex
+// doubles; the internal ones are component-major per parity.  Each CTA moves
+// a tile of TS consecutive natural rows through shared memory, so both the
+// natural rows and every internal component are read and written in
+// contiguous runs.  On a full lattice the rows lex0 .. lex0 + TS - 1 (lex0 a
+// multiple of TS) hold TS/2 sites of each parity with consecutive
+// checkerboard indices lex0/2 .. lex0/2 + TS/2 - 1: rows 2j and 2j + 1 share
+// index lex0/2 + j and have opposite parities (the lattice extents are even).
+constexpr int TS = 64;            // natural rows per tile
+constexpr int TT = 128;           // threads per tile
+constexpr int TPAD = 13;          // double2 slots per tile row of a spinor (12 + 1 against bank conflicts)
+
+// internal vector k of a site from its 12 complex components, and back
+template <int PR> struct Vec;
+template <> struct Vec<P64> {
+    static constexpr int N = 12;
+    typedef double2 T;
+    static __device__ __forceinline__ T from(const double2 *row, int k) { return row[k]; }
+    static __device__ __forceinline__ void to(T v, double2 *row, int k) { row[k] = v; }
+};
+template <> struct Vec<PDF> {
+    static constexpr int N = 12;
+    typedef df2 T;
+    static __device__ __forceinline__ T from(const double2 *row, int k) { return to_df2(row[k]); }
+    static __device__ __forceinline__ void to(T v, double2 *row, int k) { row[k] = from_df2(v); }
+};
+template <> struct Vec<P32> {
+    static constexpr int N = 6;   // two complex components per float4
+    typedef float4 T;
+    static __device__ __forceinline__ T from(const double2 *row, int k)
+    {
+        const double2 a = row[2 * k], b = row[2 * k + 1];
+        return make_float4(d2f_bits(a.x), d2f_bits(a.y), d2f_bits(b.x), d2f_bits(b.y));
+    }
+    static __device__ __forceinline__ void to(T v, double2 *row, int k)
+    {
+        row[2 * k] = make_double2(f2d_bits(v.x), f2d_bits(v.y));
+        row[2 * k + 1] = make_double2(f2d_bits(v.z), f2d_bits(v.w));
+    }
+};
+
+// row of the tile and internal site index of output item j of parity p
+// (FULL: lattice rows split by parity; else: a field of one parity, row = site)
+template <bool FULL>
+__device__ __forceinline__ int tile_row(const unsigned char *par, int j, int p)
 {
-    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (id >= 4 * g.V) return;
-    const long long lex = id >> 2;
-    const int mu = (int)(id & 3);
-    long long r = lex;
-    int c0 = (int)(r % g.L[0]); r /= g.L[0];
-    int c1 = (int)(r % g.L[1]); r /= g.L[1];
-    int c2 = (int)(r % g.L[2]); int c3 = (int)(r / g.L[2]);
-    const int parity = (c0 + c1 + c2 + c3) & 1;
-    const long long cb = lex >> 1;
-    double2 m[9];
+    return FULL ? 2 * j + (par[j] != p) : j;
+}
+
+// natural [n][12] c128 -> internal field(s): f0 (FULL: even sites), f1 (odd sites)
+template <int PR, bool FULL>
+__global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *__restrict__ nat,
+                                                         typename Vec<PR>::T *f0, typename Vec<PR>::T *f1)
+{
+    __shared__ double2 tile[TS][TPAD];
+    __shared__ unsigned char par[TS / 2];
+    const long long n = FULL ? g.V : g.Vh;
+    const long long r0 = (long long)blockIdx.x * TS;
+    const int rows = (int)(n - r0 < TS ? n - r0 : TS);
+    for (int i = threadIdx.x; i < rows * 12; i += TT) tile[i / 12][i % 12] = __ldg(nat + r0 * 12 + i);
+    if (FULL && threadIdx.x < TS / 2 && 2 * (int)threadIdx.x < rows) par[threadIdx.x] = lex_parity(g, r0 + 2 * threadIdx.x);
+    __syncthreads();
+    constexpr int NV = Vec<PR>::N, PER = FULL ? TS / 2 : TS;
+    const long long s0 = FULL ? r0 / 2 : r0;
+    if (rows == TS) {   // a whole tile: every index split below is by a constant
 #pragma unroll
-    for (int k = 0; k < 9; k++) m[k] = __ldg(U + id * 9 + k);
-    double2 *d = parity ? U64o : U64e;
+        for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * PER; w += TT) {
+            const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
+            typename Vec<PR>::T *f = p ? f1 : f0;
+            f[k * g.stride + s0 + j] = Vec<PR>::from(tile[tile_row<FULL>(par, j, p)], k);
+        }
+    } else {            // the last, partial tile (rows is even on a full lattice)
+        const int per = FULL ? rows / 2 : rows;
+        for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * per; w += TT) {
+            const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
+            typename Vec<PR>::T *f = p ? f1 : f0;
+            f[k * g.stride + s0 + j] = Vec<PR>::from(tile[tile_row<FULL>(par, j, p)], k);
+        }
+    }
+}
+
+// internal field(s) -> natural [n][12] c128
+template <int PR, bool FULL>
+__global__ void __launch_bounds__(TT) export_tile_kernel(Geom g, const typename Vec<PR>::T *__restrict__ f0,
+                                                         const typename Vec<PR>::T *__restrict__ f1, double2 *nat)
+{
+    __shared__ double2 tile[TS][TPAD];
+    __shared__ unsigned char par[TS / 2];
+    const long long n = FULL ? g.V : g.Vh;
+    const long long r0 = (long long)blockIdx.x * TS;
+    const int rows = (int)(n - r0 < TS ? n - r0 : TS);
+    if (FULL && threadIdx.x < TS / 2 && 2 * (int)threadIdx.x < rows) par[threadIdx.x] = lex_parity(g, r0 + 2 * threadIdx.x);
+    __syncthreads();
+    constexpr int NV = Vec<PR>::N, PER = FULL ? TS / 2 : TS;
+    const long long s0 = FULL ? r0 / 2 : r0;
+    if (rows == TS) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) d[(mu * 9 + k) * g.stride + cb] = m[k];
-    float4 *f = parity ? U32o : U32e;
-#pragma unroll
-    for (int k = 0; k < 3; k++)
-        f[(mu * 3 + k) * g.stride + cb] = make_float4((float)m[2 * k].x, (float)m[2 * k].y,
-                                                       (float)m[2 * k + 1].x, (float)m[2 * k + 1].y);
-    df2 *q = parity ? Udfo : Udfe;
-#pragma unroll
-    for (int k = 0; k < 9; k++) q[(mu * 9 + k) * g.stride + cb] = to_df2(m[k]);
+        for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * PER; w += TT) {
+            const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
+            const typename Vec<PR>::T *f = p ? f1 : f0;
+            Vec<PR>::to(f[k * g.stride + s0 + j], tile[tile_row<FULL>(par, j, p)], k);
+        }
+    } else {
+        const int per = FULL ? rows / 2 : rows;
+        for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * per; w += TT) {
+            const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
+            const typename Vec<PR>::T *f = p ? f1 : f0;
+            Vec<PR>::to(f[k * g.stride + s0 + j], tile[tile_row<FULL>(par, j, p)], k);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * 12; i += TT) nat[r0 * 12 + i] = tile[i / 12][i % 12];
+}
+
+// gauge links: U_nat[lex][mu][3][3] c128 -> per parity U64 [mu][9][stride]
+// double2, U32 [mu][3][stride] float4 (rows 0 and 1: 12 reals) and Udf
+// [mu][9][stride] df2; a tile of TL lattice rows (36 complex numbers each)
+constexpr int TL = 32;
+constexpr int LPAD = 37;
+__global__ void __launch_bounds__(TT) import_links_kernel(Geom g, const double2 *__restrict__ U, double2 *U64e,
+                                                          double2 *U64o, float4 *U32e, float4 *U32o, df2 *Udfe,
+                                                          df2 *Udfo)
+{
+    __shared__ double2 tile[TL][LPAD];
+    __shared__ unsigned char par[TL / 2];
+    const long long r0 = (long long)blockIdx.x * TL;
+    const int rows = (int)(g.V - r0 < TL ? g.V - r0 : TL);
+    for (int i = threadIdx.x; i < rows * 36; i += TT) tile[i / 36][i % 36] = __ldg(U + r0 * 36 + i);
+    if (threadIdx.x < TL / 2 && 2 * (int)threadIdx.x < rows) par[threadIdx.x] = lex_parity(g, r0 + 2 * threadIdx.x);
+    __syncthreads();
+    const long long s0 = r0 / 2;
+    // 36 complex entries of FP64 and df64 per site, then 12 float4 of FP32
+    auto put = [&](int j, int pk) {
+        const int p = pk / 48, k = pk % 48;
+        const double2 *row = tile[tile_row<true>(par, j, p)];
+        const long long s = s0 + j;
+        if (k < 36) {   // k = mu * 9 + entry
+            (p ? U64o : U64e)[k * g.stride + s] = row[k];
+            (p ? Udfo : Udfe)[k * g.stride + s] = to_df2(row[k]);
+        } else {        // k - 36 = mu * 3 + v: entries 2v, 2v + 1 of link mu
+            const int mu = (k - 36) / 3, v = (k - 36) % 3;
+            const double2 a = row[mu * 9 + 2 * v], b = row[mu * 9 + 2 * v + 1];
+            (p ? U32o : U32e)[(k - 36) * g.stride + s] =
+                make_float4(d2f_bits(a.x), d2f_bits(a.y), d2f_bits(b.x), d2f_bits(b.y));
+        }
+    };
+    if (rows == TL) {   // a whole tile: w splits by constants
+        for (int w = threadIdx.x; w < 2 * 48 * (TL / 2); w += TT) put(w % (TL / 2), w / (TL / 2));
+    } else {
+        const int per = rows / 2;
+        for (int w = threadIdx.x; w < 2 * 48 * per; w += TT) put(w % per, w / per);
+    }
 }
 
 void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2], void *Udf[2])
 {
     Launch L_(e, K_LAYOUT, (double)e.g.V * 4 * (144 + 144 + 48 + 144));
-    import_links_kernel<<<nblk(4 * e.g.V, 256), 256, 0, e.st>>>(
-        e.g, (const double2 *)U_nat, (double2 *)U64[0], (double2 *)U64[1], (float4 *)U32[0], (float4 *)U32[1],
-        (df2 *)Udf[0], (df2 *)Udf[1]);
+    import_links_kernel<<<nblk(e.g.V, TL), TT, 0, e.st>>>(e.g, (const double2 *)U_nat, (double2 *)U64[0],
+                                                          (double2 *)U64[1], (float4 *)U32[0], (float4 *)U32[1],
+                                                          (df2 *)Udf[0], (df2 *)Udf[1]);
 }
 
 // ---- spinors ----------------------------------------------------------------
-// natural [n][12] c128 rows -> internal component-major field
-template <typename R>
-__global__ void import_half_kernel(Geom g, const double2 *__restrict__ nat, typename St<R>::vec *f);
-
-template <>
-__global__ void import_half_kernel<double>(Geom g, const double2 *__restrict__ nat, double2 *f)
+template <int PR, bool FULL>
+static void import_t(const Exec &e, const void *nat, void *f0, void *f1)
 {
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int c = 0; c < 12; c++) f[c * g.stride + s] = __ldg(nat + s * 12 + c);
+    typedef typename Vec<PR>::T T;
+    const long long n = FULL ? e.g.V : e.g.Vh;
+    import_tile_kernel<PR, FULL><<<nblk(n, TS), TT, 0, e.st>>>(e.g, (const double2 *)nat, (T *)f0, (T *)f1);
 }
-template <>
-__global__ void import_half_kernel<float>(Geom g, const double2 *__restrict__ nat, float4 *f)
+template <int PR, bool FULL>
+static void export_t(const Exec &e, const void *f0, const void *f1, void *nat)
 {
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        double2 a = __ldg(nat + s * 12 + 2 * k), b = __ldg(nat + s * 12 + 2 * k + 1);
-        f[k * g.stride + s] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-    }
-}
-
-template <typename R>
-__global__ void export_half_kernel(Geom g, const typename St<R>::vec *__restrict__ f, double2 *nat);
-
-template <>
-__global__ void export_half_kernel<double>(Geom g, const double2 *__restrict__ f, double2 *nat)
-{
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int c = 0; c < 12; c++) nat[s * 12 + c] = __ldg(f + c * g.stride + s);
-}
-template <>
-__global__ void export_half_kernel<float>(Geom g, const float4 *__restrict__ f, double2 *nat)
-{
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        float4 t = __ldg(f + k * g.stride + s);
-        nat[s * 12 + 2 * k] = make_double2(t.x, t.y);
-        nat[s * 12 + 2 * k + 1] = make_double2(t.z, t.w);
-    }
-}
-
-__global__ void import_half_df_kernel(Geom g, const double2 *__restrict__ nat, df2 *f)
-{
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int c = 0; c < 12; c++) f[c * g.stride + s] = to_df2(__ldg(nat + s * 12 + c));
-}
-__global__ void export_half_df_kernel(Geom g, const df2 *__restrict__ f, double2 *nat)
-{
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.Vh) return;
-#pragma unroll
-    for (int c = 0; c < 12; c++) nat[s * 12 + c] = from_df2(ldg(f + c * g.stride + s));
-}
-
-__device__ __forceinline__ int lex_parity(const Geom &g, long long lex)
-{
-    long long r = lex;
-    int c0 = (int)(r % g.L[0]); r /= g.L[0];
-    int c1 = (int)(r % g.L[1]); r /= g.L[1];
-    int c2 = (int)(r % g.L[2]); int c3 = (int)(r / g.L[2]);
-    return (c0 + c1 + c2 + c3) & 1;
-}
-
-template <typename R>
-__global__ void import_full_kernel(Geom g, const double2 *__restrict__ nat, typename St<R>::vec *fe,
-                                   typename St<R>::vec *fo)
-{
-    long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (lex >= g.V) return;
-    const long long cb = lex >> 1;
-    typename St<R>::vec *f = lex_parity(g, lex) ? fo : fe;
-    if constexpr (sizeof(R) == 8) {
-#pragma unroll
-        for (int c = 0; c < 12; c++) f[c * g.stride + cb] = __ldg(nat + lex * 12 + c);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            double2 a = __ldg(nat + lex * 12 + 2 * k), b = __ldg(nat + lex * 12 + 2 * k + 1);
-            f[k * g.stride + cb] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-        }
-    }
-}
-
-template <typename R>
-__global__ void export_full_kernel(Geom g, const typename St<R>::vec *__restrict__ fe,
-                                   const typename St<R>::vec *__restrict__ fo, double2 *nat)
-{
-    long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (lex >= g.V) return;
-    const long long cb = lex >> 1;
-    const typename St<R>::vec *f = lex_parity(g, lex) ? fo : fe;
-    if constexpr (sizeof(R) == 8) {
-#pragma unroll
-        for (int c = 0; c < 12; c++) nat[lex * 12 + c] = __ldg(f + c * g.stride + cb);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            float4 t = __ldg(f + k * g.stride + cb);
-            nat[lex * 12 + 2 * k] = make_double2(t.x, t.y);
-            nat[lex * 12 + 2 * k + 1] = make_double2(t.z, t.w);
-        }
-    }
-}
-
-__global__ void import_full_df_kernel(Geom g, const double2 *__restrict__ nat, df2 *fe, df2 *fo)
-{
-    long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (lex >= g.V) return;
-    const long long cb = lex >> 1;
-    df2 *f = lex_parity(g, lex) ? fo : fe;
-#pragma unroll
-    for (int c = 0; c < 12; c++) f[c * g.stride + cb] = to_df2(__ldg(nat + lex * 12 + c));
-}
-__global__ void export_full_df_kernel(Geom g, const df2 *__restrict__ fe, const df2 *__restrict__ fo, double2 *nat)
-{
-    long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (lex >= g.V) return;
-    const long long cb = lex >> 1;
-    const df2 *f = lex_parity(g, lex) ? fo : fe;
-#pragma unroll
-    for (int c = 0; c < 12; c++) nat[lex * 12 + c] = from_df2(ldg(f + c * g.stride + cb));
+    typedef typename Vec<PR>::T T;
+    const long long n = FULL ? e.g.V : e.g.Vh;
+    export_tile_kernel<PR, FULL><<<nblk(n, TS), TT, 0, e.st>>>(e.g, (const T *)f0, (const T *)f1, (double2 *)nat);
 }
 
 void import_half(const Exec &e, int prec, const void *nat, void *f)
@@ -196,14 +213,9 @@ void import_half(const Exec &e, int prec, const void *nat, void *f)
         return;
     }
     Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P32 ? 96 : 192)));
-    if (prec == PDF) {
-        import_half_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (df2 *)f);
-        return;
-    }
-    if (prec == P64)
-        import_half_kernel<double><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (double2 *)f);
-    else
-        import_half_kernel<float><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (float4 *)f);
+    if (prec == PDF) import_t<PDF, false>(e, nat, f, nullptr);
+    else if (prec == P64) import_t<P64, false>(e, nat, f, nullptr);
+    else import_t<P32, false>(e, nat, f, nullptr);
 }
 
 void export_half(const Exec &e, int prec, const void *f, void *nat)
@@ -213,44 +225,25 @@ void export_half(const Exec &e, int prec, const void *f, void *nat)
         return;
     }
     Launch L_(e, K_LAYOUT, (double)e.g.Vh * (192 + (prec == P32 ? 96 : 192)));
-    if (prec == PDF) {
-        export_half_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const df2 *)f, (double2 *)nat);
-        return;
-    }
-    if (prec == P64)
-        export_half_kernel<double><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const double2 *)f, (double2 *)nat);
-    else
-        export_half_kernel<float><<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)f, (double2 *)nat);
+    if (prec == PDF) export_t<PDF, false>(e, f, nullptr, nat);
+    else if (prec == P64) export_t<P64, false>(e, f, nullptr, nat);
+    else export_t<P32, false>(e, f, nullptr, nat);
 }
 
 void import_full(const Exec &e, int prec, const void *nat, void *fe, void *fo)
 {
     Launch L_(e, K_LAYOUT, (double)e.g.V * (192 + (prec == P32 ? 96 : 192)));
-    if (prec == PDF) {
-        import_full_df_kernel<<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (df2 *)fe, (df2 *)fo);
-        return;
-    }
-    if (prec == P64)
-        import_full_kernel<double><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (double2 *)fe,
-                                                                       (double2 *)fo);
-    else
-        import_full_kernel<float><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)nat, (float4 *)fe,
-                                                                      (float4 *)fo);
+    if (prec == PDF) import_t<PDF, true>(e, nat, fe, fo);
+    else if (prec == P64) import_t<P64, true>(e, nat, fe, fo);
+    else import_t<P32, true>(e, nat, fe, fo);
 }
 
 void export_full(const Exec &e, int prec, const void *fe, const void *fo, void *nat)
 {
     Launch L_(e, K_LAYOUT, (double)e.g.V * (192 + (prec == P32 ? 96 : 192)));
-    if (prec == PDF) {
-        export_full_df_kernel<<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const df2 *)fe, (const df2 *)fo, (double2 *)nat);
-        return;
-    }
-    if (prec == P64)
-        export_full_kernel<double><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const double2 *)fe,
-                                                                       (const double2 *)fo, (double2 *)nat);
-    else
-        export_full_kernel<float><<<nblk(e.g.V, 256), 256, 0, e.st>>>(e.g, (const float4 *)fe,
-                                                                      (const float4 *)fo, (double2 *)nat);
+    if (prec == PDF) export_t<PDF, true>(e, fe, fo, nat);
+    else if (prec == P64) export_t<P64, true>(e, fe, fo, nat);
+    else export_t<P32, true>(e, fe, fo, nat);
 }
 
 // ---- conversion and gamma_5 -------------------------------------------------
@@ -261,7 +254,7 @@ __global__ void d2f_kernel(Geom g, const double2 *__restrict__ in, float4 *out)
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         double2 a = __ldg(in + (2 * k) * g.stride + s), b = __ldg(in + (2 * k + 1) * g.stride + s);
-        out[k * g.stride + s] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        out[k * g.stride + s] = make_float4(d2f_bits(a.x), d2f_bits(a.y), d2f_bits(b.x), d2f_bits(b.y));
     }
 }
 __global__ void f2d_kernel(Geom g, const float4 *__restrict__ in, double2 *out)
@@ -271,8 +264,8 @@ __global__ void f2d_kernel(Geom g, const float4 *__restrict__ in, double2 *out)
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         float4 t = __ldg(in + k * g.stride + s);
-        out[(2 * k) * g.stride + s] = make_double2(t.x, t.y);
-        out[(2 * k + 1) * g.stride + s] = make_double2(t.z, t.w);
+        out[(2 * k) * g.stride + s] = make_double2(f2d_bits(t.x), f2d_bits(t.y));
+        out[(2 * k + 1) * g.stride + s] = make_double2(f2d_bits(t.z), f2d_bits(t.w));
     }
 }
 
@@ -336,13 +329,14 @@ void convert(const Exec &e, int from, const void *in, int to, void *out)
 }
 
 // gamma_5 = diag(1, 1, -1, -1): negate the components of spins 2 and 3
-// (the last half of the vectors of a site in either precision)
+// (the last half of the vectors of a site in either precision); in place, the
+// first half is left untouched
 __global__ void gamma5_d_kernel(Geom g, const double2 *in, double2 *out)
 {
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
+    for (int k = in == out ? 6 : 0; k < 12; k++) {
         double2 t = in[k * g.stride + s];
         if (k >= 6) t = make_double2(-t.x, -t.y);
         out[k * g.stride + s] = t;
@@ -353,7 +347,7 @@ __global__ void gamma5_f_kernel(Geom g, const float4 *in, float4 *out)
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
+    for (int k = in == out ? 3 : 0; k < 6; k++) {
         float4 t = in[k * g.stride + s];
         if (k >= 3) t = make_float4(-t.x, -t.y, -t.z, -t.w);
         out[k * g.stride + s] = t;
@@ -365,7 +359,7 @@ __global__ void gamma5_df_kernel(Geom g, const float4 *in, float4 *out)
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.Vh) return;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
+    for (int k = in == out ? 6 : 0; k < 12; k++) {
         float4 t = in[k * g.stride + s];
         if (k >= 6) t = make_float4(-t.x, -t.y, -t.z, -t.w);
         out[k * g.stride + s] = t;
@@ -378,7 +372,7 @@ void gamma5(const Exec &e, int prec, const void *in, void *out)
         bf16_gamma5(e, in, out);
         return;
     }
-    Launch L_(e, K_LAYOUT, (double)e.g.Vh * 2 * (prec == P32 ? 96 : 192));
+    Launch L_(e, K_LAYOUT, (double)e.g.Vh * (in == out ? 1 : 2) * (prec == P32 ? 96 : 192));
     if (prec == PDF) {
         gamma5_df_kernel<<<nblk(e.g.Vh, 256), 256, 0, e.st>>>(e.g, (const float4 *)in, (float4 *)out);
         return;

@@ -112,6 +112,53 @@ __device__ __forceinline__ df64 operator/(df64 a, df64 b)
     return df_fast2sum(q1, q2);
 }
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
+// Conversions between double and df64 / float with integer bit operations
+// (GB300's FP64 pipe, which float <-> double conversions and double adds
+// use, runs at 1/64 of the FP32 rate, so field import and export would
+// otherwise be bound by it).  For a normal double d with exponent e and 53-bit
+// significand m: hi = m's top 24 bits rounded to nearest even, and the
+// remainder m - hi, an integer R with |R| <= 2^28 in units of 2^(e-52), gives
+// lo = RN(R) 2^(e-52) -- the same values as hi = (float)d, lo = (float)(d - hi).
+// Zero, subnormal, very small or very large magnitudes and non-finite values
+// take the FP64 route.
+__device__ __forceinline__ df64 df_split(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -74 || e > 126) return df64(d);
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned q = (unsigned)(m >> 29);             // 2^23 <= q < 2^24
+    int R = (int)(m & 0x1FFFFFFFull);             // 0 <= R < 2^29
+    if (R > (1 << 28) || (R == (1 << 28) && (q & 1u))) {
+        q += 1;
+        R -= 1 << 29;
+    }
+    int eh = e;
+    if (q == (1u << 24)) {
+        q >>= 1;
+        eh += 1;
+    }
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)(eh + 127) << 23) | (q & 0x7FFFFFu));
+    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);   // 2^(e-52), normal for e >= -74
+    return df64(hi, __int2float_rn(sign ? -R : R) * scale);
+}
+// (float)d, rounded to nearest even
+__device__ __forceinline__ float d2f_bits(double d) { return df_split(d).hi; }
+// (double)x, exact
+__device__ __forceinline__ double f2d_bits(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned E = (b >> 23) & 0xFFu;
+    if (E == 0u && (b & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
+    if (E == 0u || E == 0xFFu) return (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                            ((unsigned long long)(E + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+// hi + lo as a double (one FP64 add)
+__device__ __forceinline__ double df_join(float hi, float lo) { return f2d_bits(hi) + f2d_bits(lo); }
+
 __device__ __forceinline__ bool df_positive(df64 a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 

@@ -106,13 +106,15 @@ void gamma5(const Exec &e, int prec, const void *in, void *out);
 
 // ---- clover (clover.cu) ----------------------------------------------------
 // C(x) of every site from the internal df64 links: packed blocks per parity in
-// df64 and, rounded, FP64 and FP32; Fscratch: device scratch of 6 * 9 * V * 8
-// bytes (the six field strengths)
-void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C64[2],
-                  void *C32[2], void *Fscratch);
-// inverse of the blocks of one parity by LDL^+ in df64, written in df64, FP64
-// and FP32; *flag += failures
-void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci64, void *Ci32, int *flag);
+// df64 and, rounded, FP32; Fscratch: device scratch of 6 * 9 * V * 8 bytes
+// (the six field strengths)
+void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C32[2],
+                  void *Fscratch);
+// inverse of the blocks of one parity by LDL^+ in df64, written in df64 and
+// FP32; *flag += failures
+void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci32, int *flag);
+// FP64 copy of one parity's df64 blocks (both 6x6 blocks), rounded
+void clover_to_f64(const Exec &e, const void *Cdf, void *C64);
 // natural export: out[V][2][6][6] c128 from FP64 packed blocks (null parity pointer -> zeros)
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out);
 
