@@ -60,6 +60,7 @@ struct lq_ctx {
     RedScratch red{};
     double *h_pin = nullptr;   // pinned host mirror of red.out / coefficients
     double *d_coef = nullptr;  // device coefficients [2 * RED_SLOTS]
+    double *d_s2 = nullptr;    // device: squared scales s_j^2 of the FP32 GMRES basis [RED_SLOTS]
     std::map<std::string, std::pair<void *, size_t>> ws;
     std::vector<void *> owned;
     std::string err;
@@ -409,6 +410,41 @@ double arnoldi_cgs2(lq_ctx *c, int prec, void *V, int k, void *w, Hess &H)
     return std::sqrt(nrm2);
 }
 
+// The FP32 GMRES keeps its basis unnormalised: v_j = s_j V_j with the scales
+// s_j on the host, which saves the pass that would scale each new vector by
+// 1 / ||w||.  set_scale stages s_j^2 for the device-side CGS coefficients
+// (each slot is written once per cycle; the stream has synchronised since its
+// previous copy, at every Arnoldi step's fetch).
+void set_scale(lq_ctx *c, int j, double s)
+{
+    c->h_pin[4 * RED_SLOTS + j] = s * s;
+    ck(c, cudaMemcpyAsync(c->d_s2 + j, c->h_pin + 4 * RED_SLOTS + j, sizeof(double), cudaMemcpyHostToDevice, c->st),
+       "cudaMemcpyAsync H2D");
+}
+
+// Arnoldi step on the unnormalised FP32 basis: w = D_S V_k = D_S v_k / s_k.
+// In the v's, h_jk = (v_j, D_S v_k) = s_j s_k (V_j, w) and CGS removes
+// sum_j h_jk v_j, i.e. w -= sum_j s_j^2 (V_j, w) V_j (the reduction applies
+// s_j^2); the new vector V_{k+1} = w has s_{k+1} = 1 / ||w||, and the true
+// h_{k+1,k} = s_k ||w||, which is returned.
+double arnoldi_scaled(lq_ctx *c, void *V, int k, void *w, Hess &H, double *s)
+{
+    Exec e = c->ex();
+    const int n = k + 1;
+    multi_dot(e, P32, V, n, w, c->red, 0);
+    reduce_finish(e, c->red, 0, n, c->d_s2);
+    multi_axpy(e, P32, V, n, c->red.out, -1, w, &c->red, n);
+    reduce_finish(e, c->red, n, 1);
+    ck_launch(c, "arnoldi");
+    const double *hv = fetch(c, 0, n + 1);
+    for (int j = 0; j < n; j++) H.h(j, k) = cd(hv[2 * j], hv[2 * j + 1]) * (s[k] / s[j]);
+    const double nrm2 = hv[2 * n];
+    if (!std::isfinite(nrm2)) fail(c, LQ_ERR_NAN, "NaN/Inf in the Arnoldi process");
+    const double nrm = std::sqrt(nrm2);
+    s[k + 1] = nrm > 0 ? 1.0 / nrm : 0.0;
+    return s[k] * nrm;
+}
+
 // Restarted GMRES(m) on D_S in precision `prec`: b, x internal even fields.
 // x_zero: x is known to be zero on entry (skips the first residual product).
 // tol > 0 stops at ||b - D_S x|| <= tol ||b||; tol == 0 runs max_cycles full cycles.
@@ -445,13 +481,21 @@ KResult gmres(lq_ctx *c, int prec, const void *b, void *x, int m, int max_cycles
             return R;
         }
         R.cycles++;
-        axpby(e, prec, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
+        // FP32: v0 = s_0 V_0 kept unnormalised; otherwise normalised in place
+        const bool scaled = prec == P32;
+        double s[MAX_RESTART + 1];
+        if (scaled) {
+            s[0] = 1.0 / beta;
+            set_scale(c, 0, s[0]);
+        } else {
+            axpby(e, prec, 0.0, 0.0, v0, 1.0 / beta, 0.0, v0);
+        }
         H.reset(beta);
         int nk = 0;
         for (int k = 0; k < m; k++) {
             void *w = vec_at(c, prec, V, k + 1);
             op_schur(c, prec, vec_at(c, prec, V, k), w, t);
-            const double hk1 = arnoldi_cgs2(c, prec, V, k, w, H);
+            const double hk1 = scaled ? arnoldi_scaled(c, V, k, w, H, s) : arnoldi_cgs2(c, prec, V, k, w, H);
             double colnorm2 = hk1 * hk1;
             for (int j = 0; j <= k; j++) colnorm2 += std::norm(H.h(j, k));
             H.h(k + 1, k) = hk1;
@@ -461,9 +505,12 @@ KResult gmres(lq_ctx *c, int prec, const void *b, void *x, int m, int max_cycles
             R.relres = est / bnorm;
             const bool breakdown = hk1 <= 1e-14 * std::sqrt(colnorm2);
             if (breakdown || (tol > 0 && est <= tol * bnorm) || k == m - 1) break;
-            axpby(e, prec, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
+            if (scaled) set_scale(c, k + 1, s[k + 1]);
+            else axpby(e, prec, 0.0, 0.0, w, 1.0 / hk1, 0.0, w);
         }
         std::vector<cd> y = H.solve(nk);
+        if (scaled)   // x += sum_j y_j v_j = sum_j (y_j s_j) V_j
+            for (int j = 0; j < nk; j++) y[j] *= s[j];
         upload_coef(c, y);
         multi_axpy(e, prec, V, nk, c->d_coef, +1, x, nullptr, 0);
         ck_launch(c, "gmres update");
@@ -1250,8 +1297,10 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
         c->red.partial = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS * c->red.blocks);
         c->red.out = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
         c->d_coef = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
+        c->d_s2 = (double *)dev_alloc(c, sizeof(double) * RED_SLOTS);
         c->dflag = (int *)dev_alloc(c, sizeof(int));
-        ck(c, cudaMallocHost((void **)&c->h_pin, sizeof(double) * 4 * RED_SLOTS), "cudaMallocHost");
+        // pinned: [0, 2R) red.out mirror, [2R, 4R) coefficients, [4R, 5R) basis scales
+        ck(c, cudaMallocHost((void **)&c->h_pin, sizeof(double) * 5 * RED_SLOTS), "cudaMallocHost");
     } catch (const Fail &f) {
         lq_destroy(c);
         return f.s;

@@ -181,16 +181,17 @@ __global__ void __launch_bounds__(RT) nat_norm2_kernel(const double2 *__restrict
     }
 }
 
-// one block per value: out[v] = sum_b partial[b][v] in a fixed tree order
+// one block per value: out[v] = sum_b partial[b][v] in a fixed tree order,
+// times scale[v / 2] when a scale (one real per complex value) is given
 __global__ void __launch_bounds__(RT) reduce_finish_kernel(const double *__restrict__ partial, int blocks, int pitch,
-                                                           double *out)
+                                                           const double *__restrict__ scale, double *out)
 {
     __shared__ double sh[RT / 32];
     const int v = blockIdx.x;
     double acc[1] = {0.0};
     for (int b = threadIdx.x; b < blocks; b += RT) acc[0] += partial[(long long)b * pitch + v];
     block_sum<double, 1>(acc, sh);
-    if (threadIdx.x == 0) out[v] = acc[0];
+    if (threadIdx.x == 0) out[v] = scale ? acc[0] * scale[v >> 1] : acc[0];
 }
 
 // y = a x + b y
@@ -449,11 +450,12 @@ void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch
     nat_norm2_kernel<<<r.blocks, RT, 0, e.st>>>((const double2 *)v, n_sites * 12, r.partial, pitch, slot);
 }
 
-void reduce_finish(const Exec &e, const RedScratch &r, int first, int count)
+void reduce_finish(const Exec &e, const RedScratch &r, int first, int count, const double *scale)
 {
     if (count <= 0) return;
     Launch L_(e, K_FINISH, (double)r.blocks * 2 * count * 8.0);
-    reduce_finish_kernel<<<2 * count, RT, 0, e.st>>>(r.partial + 2 * first, r.blocks, 2 * r.maxv, r.out + 2 * first);
+    reduce_finish_kernel<<<2 * count, RT, 0, e.st>>>(r.partial + 2 * first, r.blocks, 2 * r.maxv, scale,
+                                                     r.out + 2 * first);
 }
 
 }  // namespace lq

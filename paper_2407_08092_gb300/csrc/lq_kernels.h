@@ -230,8 +230,10 @@ void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, co
                int slot0);
 // ||w||^2 into slot `slot` (real part)
 void norm2(const Exec &e, int prec, const void *w, const RedScratch &r, int slot);
-// sum the per-block partials of slots [first, first + count) into r.out
-void reduce_finish(const Exec &e, const RedScratch &r, int first, int count);
+// sum the per-block partials of slots [first, first + count) into r.out; with
+// `scale` (device, one real per slot, indexed from slot `first`) each complex
+// result j is multiplied by scale[j]
+void reduce_finish(const Exec &e, const RedScratch &r, int first, int count, const double *scale = nullptr);
 // norm of a natural c128 field of n sites (used by lq_norm2)
 void nat_norm2(const Exec &e, const void *v, long long n_sites, const RedScratch &r, int slot);
 int reduction_blocks(const Geom &g);

@@ -290,3 +290,29 @@ def test_nan_and_not_converged(lqdd):
         assert ei.value.status == lqdd.LQ_ERR_ARG
     finally:
         p.close()
+
+
+def test_set_gauge_refreshes_the_copies_made_on_first_use():
+    """The FP64 clover blocks and the BF16 links are rounded from the df64 /
+    FP32 copies when an FP64 or BF16 operator first needs them; a new gauge
+    field must replace them too."""
+    from paper_2407_08092_gb300 import lqdd
+    L = (4, 4, 4, 8)
+    p = Pair(L, eps=0.25, seed=1400, m0=0.05, csw=1.0)
+    try:
+        x = synth.gaussian_spinor(p.Vh, 81)
+        # build both copies on the first field
+        assert rel(p.apply(lqdd.LQ_OP_SCHUR, lqdd.LQ_F64, x), p.lat.schur(x)) < 1e-12
+        assert rel(p.apply(lqdd.LQ_OP_SCHUR, lqdd.LQ_BF16, x), p.lat.schur(x)) < 1e-2
+        U2 = synth.gauge_links(L, 0.3, 1401)
+        lat2 = oracle.Lattice(L, U2, m0=0.05, csw=1.0, t_bc=-1)
+        lqdd.lq_set_gauge(p.ctx, p.torch.from_numpy(U2).cuda())
+        want = lat2.schur(x)
+        assert rel(want, p.lat.schur(x)) > 1e-2          # the two fields give different operators
+        assert rel(p.apply(lqdd.LQ_OP_SCHUR, lqdd.LQ_F64, x), want) < 1e-12
+        assert rel(p.apply(lqdd.LQ_OP_SCHUR, lqdd.LQ_BF16, x), want) < 1e-2
+        out = p.torch.zeros((p.V, 2, 6, 6), dtype=p.torch.complex128, device="cuda")
+        lqdd.lq_export_clover(p.ctx, 0, out)
+        assert rel(p.host(out), blocks_of(lat2.C)) < 1e-13
+    finally:
+        p.close()
