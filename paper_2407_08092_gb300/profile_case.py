@@ -102,10 +102,20 @@ def main():
         p = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
                              max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
                              smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+        lqdd.lq_solve(ctx, p, b, x)
+        lqdd.lq_profile(ctx, 1)
         for _ in range(a.apps):
             x.zero_()
             status, st = lqdd.lq_solve(ctx, p, b, x)
             assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
+        torch.cuda.synchronize()
+        print("mixed solve", round(st.time_ms, 2), "ms", st.iters, "outer", st.inner_iters, "inner")
+        for c in range(lqdd.LQ_K_COUNT):
+            nl, ms, by, fl = lqdd.lq_profile_read(ctx, c)
+            if nl:
+                print(f"{lqdd.lq_kernel_class_name(c):14s} {nl:5d} launches {1e3 * ms / nl:9.2f} us/launch "
+                      f"{by / (ms * 1e6):8.1f} GB/s")
+        lqdd.lq_profile(ctx, 0)
         out = st.rel_resid_true
     torch.cuda.synchronize()
     print("ok", L, a.mode, "prec", a.prec, "apps", a.apps, out)
