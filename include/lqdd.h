@@ -133,10 +133,13 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream);
 lq_status lq_destroy(lq_ctx *ctx);
 
 /* Load a gauge field (device U[V][4][3][3], complex double, natural order) and
- * build from it, on the device: the internal FP64 and FP32 link copies, the
- * clover term C(x) of every site (Sec. 2.3) and the inverse D_oo^{-1} of the odd
- * blocks (6x6 Hermitian blocks, Sec. 2.4.5).  Links are expected to be SU(3);
- * the FP32 copy keeps two rows and rebuilds the third as conj(r1 x r2).
+ * build from it, on the device: the internal FP64, FP32 and df64 link copies,
+ * the clover term C(x) of every site (Sec. 2.3) and the inverse D_oo^{-1} of
+ * the odd blocks (6x6 Hermitian blocks, Sec. 2.4.5), both in df64 and FP32.
+ * The FP64 clover copies and the BF16 links are rounded from these when an
+ * FP64 or BF16 operator (or lq_export_clover) first needs them after the call.
+ * Links are expected to be SU(3); the FP32 and BF16 copies keep two rows and
+ * rebuild the third as conj(r1 x r2).  The caller's U may be freed on return.
  * Synchronises; LQ_ERR_BREAKDOWN if a clover block has a non-positive pivot. */
 lq_status lq_set_gauge(lq_ctx *ctx, const void *U);
 
@@ -293,7 +296,7 @@ typedef enum {
     LQ_K_HOP_K2_F64,     /* K2: y_e = D_ee x_e - D_eo t_o (and its fused Richardson form), FP64 */
     LQ_K_HOP_K2_F32,     /* K2, FP32 */
     LQ_K_HOP_OTHER,      /* full-lattice D, prepare, reconstruct, clover apply */
-    LQ_K_CLOVER,         /* clover assembly from the field strengths, inverse, rounded copies, export */
+    LQ_K_CLOVER,         /* clover assembly from the field strengths, inverse (df64 and FP32), export */
     LQ_K_LAYOUT,         /* natural <-> internal layout, precision conversion, gamma5 */
     LQ_K_DOT_F64, LQ_K_DOT_F32,    /* multi-dot products */
     LQ_K_AXPY_F64, LQ_K_AXPY_F32,  /* axpby / multi-axpy */
