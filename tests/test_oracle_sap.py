@@ -11,7 +11,13 @@
 * an exact red sweep leaves a zero residual on every red block, and the red
   blocks' solves do not depend on their order;
 * one block covering the lattice turns SAP(1, many) into D^{-1} b;
-* SAP lowers the residual as n grows.
+* SAP lowers the residual as n grows;
+* after a colour's block solves (inexact, m MR steps), the whole operator's
+  residual on a block of that colour is the MR residual of the block's Schur
+  system on the even sites and zero on the odd sites, and on the other
+  colour's blocks it changed only by the hops of the correction across the
+  block faces -- the identities that let the GPU path keep the residual block
+  by block instead of applying D to the whole lattice before every colour.
 """
 import numpy as np
 import pytest
@@ -162,3 +168,29 @@ def test_sap_reduces_the_residual():
         x = osap.sap(lat, b, n, 4, (4, 4, 2, 2))
         res.append(np.linalg.norm(b - lat.dirac(x)) / np.linalg.norm(b))
     assert res[0] < 0.5 and res[1] < res[0] and res[2] < res[1], res
+
+
+@pytest.mark.parametrize("L,block", [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 4, 4), (4, 2, 4, 2))])
+def test_colour_sweep_residual_is_blockwise(L, block):
+    lat = lattice(L, seed=11)
+    blocks = osap.Blocks(L, block)
+    ops = [osap.BlockOperator(lat, blocks, k) for k in range(blocks.count)]
+    b = synth.gaussian_spinor(lat.V, 12).reshape(lat.V, 4, 3)
+    x0 = 0.1 * synth.gaussian_spinor(lat.V, 13).reshape(lat.V, 4, 3)   # an earlier iterate
+    r = b - lat.dirac(x0)
+    e = np.zeros_like(b)
+    for k in blocks.of_colour(osap.RED):
+        e = e + ops[k].solve(r, 3)
+    r1 = b - lat.dirac(x0 + e)
+    tol = 1e-12 * np.abs(b).max()
+    for k in blocks.of_colour(osap.RED):
+        op = ops[k]
+        rhat = op.even * r - op.D_eo(op.D_oo_inv(op.odd * r))
+        mr_residual = rhat - op.schur(op.even * e)
+        assert np.abs(op.even * r1 - mr_residual).max() < tol
+        assert np.abs(op.odd * r1).max() < tol
+    black = np.isin(blocks.block_of, blocks.of_colour(osap.BLACK))[:, None, None]
+    # e vanishes on the black sites, so D e there is the hop term alone: -1/2 hop(e)
+    assert np.abs(black * (r1 - (r + 0.5 * lat.hop(e)))).max() < tol
+    # and only sites with a red neighbour across a face change
+    assert np.abs(black * (r1 - r)).max() > 1e-3 * np.abs(b).max()
