@@ -204,6 +204,47 @@ def test_clover_abelian_closed_form():
     assert np.abs(lat0.C - (4 + m0) * np.eye(12)[None]).max() < 1e-15
 
 
+def test_clover_from_paired_leaves():
+    """C(x) rebuilt from the field strength written with the leaves paired by a
+    shared link (only F = (Q - Q^+)/8 is needed, so with AH(M) = M - M^+:
+    F = [AH(U_mu(x) (A - B)) + AH((C' - D') U_mu(x - mu))] / 8, where
+    L1 = U_mu(x) A, L4^+ = U_mu(x) B, L2 = C' U_mu(x - mu), L3^+ = D' U_mu(x - mu))
+    and C = (4 + m0) + c_sw (i/2) sum_{mu<nu} sigma_mu_nu (x) F_mu_nu equals the
+    oracle's clover term, which sums the four leaves directly."""
+    L = (4, 4, 2, 6)
+    lat = rand_lattice(L, seed=43, eps=0.7, csw=1.3)
+    U, c = lat.U, coords(L)
+    dag = lambda m: np.conj(np.swapaxes(m, -1, -2))
+
+    def at(d, mu):   # U_mu at x + d for every site x
+        cc = (c + np.asarray(d)) % np.asarray(L)
+        return U[cc[:, 0] + L[0] * (cc[:, 1] + L[1] * (cc[:, 2] + L[2] * cc[:, 3])), mu]
+
+    def e(mu, k=1):
+        v = np.zeros(4, dtype=int)
+        v[mu] = k
+        return v
+
+    mm = lambda *ms: ms[0] if len(ms) == 1 else np.einsum("nab,nbc->nac", ms[0], mm(*ms[1:]))
+    g = [oracle.gamma(mu) for mu in range(4)]
+    C = np.zeros((lat.V, 12, 12), dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            m, n = e(mu), e(nu)
+            A = mm(at(m, nu), dag(at(n, mu)), dag(at(0 * m, nu)))
+            B = mm(dag(at(m - n, nu)), dag(at(-n, mu)), at(-n, nu))
+            Cp = mm(at(0 * m, nu), dag(at(n - m, mu)), dag(at(-m, nu)))
+            Dp = mm(dag(at(-n, nu)), dag(at(-m - n, mu)), at(-m - n, nu))
+            M1 = mm(at(0 * m, mu), A - B)
+            M2 = mm(Cp - Dp, at(-m, mu))
+            F = (M1 - dag(M1) + M2 - dag(M2)) / 8
+            sigma = 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+            C += 0.5j * lat.csw * np.einsum("st,nab->nsatb", sigma, F).reshape(lat.V, 12, 12)
+    C += (4 + lat.m0) * np.eye(12)
+    assert np.abs(C - lat.C).max() < 1e-13
+    assert np.abs(lat.C - (4 + lat.m0) * np.eye(12)).max() > 1e-2
+
+
 def test_clover_structure_and_inverse():
     """C is Hermitian, commutes with g5 (two 6x6 blocks), and C C^{-1} = 1."""
     lat = rand_lattice((4, 4, 4, 2), seed=41, eps=0.9, csw=1.9)
