@@ -97,7 +97,10 @@ typedef struct {
                             the FGMRES outer iteration (LQ_F64 or LQ_DF64), and prepare,
                             reconstruct and the true residual (LQ_F64 or LQ_DF64; LQ_F32 selects
                             LQ_F64 there) */
-    double tol;          /* stop when ||b_hat_e - D_S x_e|| <= tol ||b_hat_e|| (recomputed) */
+    double tol;          /* relative residual of the full system, ||b - D x|| <= tol ||b||: after the
+                            reconstruction of Eq. 2 the odd residual vanishes and the even one is
+                            b_hat_e - D_S x_e, so the Schur solve stops when
+                            ||b_hat_e - D_S x_e|| <= tol ||b|| (recomputed, FP64-class) */
     int restart;         /* Krylov length m of each cycle, 1..256 */
     int max_restarts;    /* maximum number of cycles, >= 1 */
     int smoother;        /* lq_smoother_kind: preconditioner of FGMRES, or the method of lq_smooth */
@@ -116,7 +119,7 @@ typedef struct {
     int cycles;              /* restart cycles of the (outer) solver */
     int iters;               /* Arnoldi steps of the (outer) solver */
     long long inner_iters;   /* D_S applications inside smoother / preconditioner calls */
-    double rel_resid;        /* ||b_hat_e - D_S x_e|| / ||b_hat_e|| at exit, recomputed in FP64 */
+    double rel_resid;        /* ||b_hat_e - D_S x_e|| / ||b|| at exit, recomputed in FP64 or df64 */
     double rel_resid_true;   /* ||b - D x|| / ||b|| on the full lattice, FP64 */
     double time_ms;          /* host wall time of the call */
     double bytes;            /* algorithmic bytes of every kernel the call launched */
@@ -193,7 +196,7 @@ lq_status lq_solve(lq_ctx *ctx, const lq_solver_params *params, const void *b, v
  * sides as the cache-friendly extension: here every operator launch applies D_S
  * to all right-hand sides, reading each site's links and clover block once.
  * Method: odd-even reduction (Eq. 2) per right-hand side, then defect correction
- * in df64 -- R = b_hat - D_S x, stop when ||R_r|| <= tol ||b_hat_r|| for every r --
+ * in df64 -- R = b_hat - D_S x, stop when ||R_r|| <= tol ||b_r|| for every r --
  * whose corrections come from batched GMRES(m) in FP32 (Algorithm 2 per right-hand
  * side, Givens least squares on the device, one CUDA-graph replay per cycle) run to
  * a relative residual of smooth_tol or smooth_n cycles.

@@ -655,8 +655,10 @@ long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void
 }
 
 // Flexible GMRES(m) in precision W (FP64 or df64), right-preconditioned by the
-// smoother in inner_prec
-KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, long long *inner_iters)
+// smoother in inner_prec.  Stops at ||b - D_S x|| <= tol * bnorm_ref (bnorm_ref < 0:
+// the norm of b itself).
+KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, long long *inner_iters,
+               double bnorm_ref = -1.0)
 {
     Exec e = c->ex();
     KResult R;
@@ -668,7 +670,7 @@ KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lon
     void *t = field(c, W, "outer:t");
     void *vq = q == W ? nullptr : field(c, q, "prec:v");
     void *zq = q == W ? nullptr : field(c, q, "prec:z");
-    const double bnorm = std::sqrt(norm2_of(c, W, b));
+    const double bnorm = bnorm_ref >= 0 ? bnorm_ref : std::sqrt(norm2_of(c, W, b));
     if (!std::isfinite(bnorm)) fail(c, LQ_ERR_NAN, "NaN/Inf in the right-hand side");
     if (bnorm == 0.0) {
         zero(e, W, x);
@@ -1533,20 +1535,29 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
         import_full(e, W, b, be, bo);
         import_full(e, W, x, xe, xo);
         op_prepare(c, W, be, bo, bh, t);
+        // The tolerance is on the full system, ||b - D x|| <= tol ||b||.  After the
+        // reconstruction of Eq. 2 the odd residual vanishes and the even one is
+        // b_hat_e - D_S x_e, so the Schur solve is measured against ||b||, not ||b_hat_e||.
+        norm2(e, W, be, c->red, 0);
+        norm2(e, W, bo, c->red, 1);
+        reduce_finish(e, c->red, 0, 2);
+        ck_launch(c, "norm of b");
+        const double *hb = fetch(c, 0, 2);
+        const double bfull = std::sqrt(hb[0] + hb[2]);
         KResult R;
         long long inner = 0;
         if (p->solver == LQ_SOLVER_GMRES) {
             if (p->prec != LQ_F32) {
-                R = gmres(c, W, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV");
+                R = gmres(c, W, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV", bfull);
             } else {
                 void *bq = field(c, P32, "sol:bq"), *xq = field(c, P32, "sol:xq");
                 convert(e, W, bh, P32, bq);
                 convert(e, W, xe, P32, xq);
-                R = gmres(c, P32, bq, xq, p->restart, p->max_restarts, p->tol, false, "outerV");
+                R = gmres(c, P32, bq, xq, p->restart, p->max_restarts, p->tol, false, "outerV", bfull);
                 convert(e, P32, xq, W, xe);
             }
         } else {
-            R = fgmres(c, p, bh, xe, &inner);
+            R = fgmres(c, p, bh, xe, &inner, bfull);
         }
         op_reconstruct(c, W, bo, xe, xo);
         export_full(e, W, xe, xo, x);
@@ -1749,8 +1760,13 @@ lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rh
             out.resize(N);
             for (int k = 0; k < N; k++) out[k] = std::sqrt(G->h[2 * N + k]);
         };
-        std::vector<double> bn, rn;
-        norms(&MW::BH, bn);
+        // reference norm of each system: its full right-hand side, so that the stop
+        // ||b_hat - D_S x|| <= tol ||b|| is the full system's relative residual after
+        // the reconstruction of Eq. 2 (the odd residual vanishes there)
+        std::vector<double> bn, bo_n, rn;
+        norms(&MW::BE, bn);
+        norms(&MW::BO, bo_n);
+        for (int k = 0; k < N; k++) bn[k] = std::sqrt(bn[k] * bn[k] + bo_n[k] * bo_n[k]);
         std::vector<int> outer(N, 0);
         std::vector<long long> inner(N, 0);
         bool all = false;

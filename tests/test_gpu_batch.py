@@ -43,7 +43,7 @@ def test_solve_batch_against_oracle(L, n):
         xs = p.host(x)
         for r in range(n):
             r_true = np.linalg.norm(b[r] - p.lat.dirac(xs[r])) / np.linalg.norm(b[r])
-            assert r_true <= 2e-10, (r, r_true)
+            assert r_true <= 1e-10, (r, r_true)
             assert abs(r_true - stats[r].rel_resid_true) <= 1e-3 * r_true + 1e-15
             assert stats[r].rel_resid <= 1e-10
         # the solutions themselves against the oracle's odd-even GMRES
@@ -127,7 +127,7 @@ def test_solve_group_uneven_lattices():
                 xh = p.host(x)
                 for r in range(b.shape[0]):
                     r_true = np.linalg.norm(b[r] - p.lat.dirac(xh[r])) / np.linalg.norm(b[r])
-                    assert r_true <= 2e-10, (p.L, r, r_true)
+                    assert r_true <= 1e-10, (p.L, r, r_true)
                     assert abs(r_true - stats[k].rel_resid_true) <= 1e-3 * r_true + 1e-15
                     k += 1
             spt, rpt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
@@ -147,7 +147,7 @@ def test_solve_group_uneven_lattices():
             for p, b, x in zip(pairs, bs, xs2):
                 xh = p.host(x)
                 for r in range(b.shape[0]):
-                    assert np.linalg.norm(b[r] - p.lat.dirac(xh[r])) / np.linalg.norm(b[r]) <= 2e-10
+                    assert np.linalg.norm(b[r] - p.lat.dirac(xh[r])) / np.linalg.norm(b[r]) <= 1e-10
         # the same systems one member at a time (lq_solve_batch) give the same solutions
         for p, d, x in zip(pairs, db, xs):
             x1 = p.torch.zeros_like(d)
@@ -186,3 +186,43 @@ def test_solve_group_status_codes():
     finally:
         a.close()
         b.close()
+
+
+def test_full_size_batched_workload():
+    """The full batched workload: 12 spin-colour point sources at the origin on
+    each of 24^3 x 48, 8^4, 16^4 and 16^3 x 32 (own links, eps 0.25, m0 0.05,
+    c_sw 1; link seeds 1103, 1101, 1102, 1104), 48 systems in one lq_solve_group
+    with the benchmark's parameters (inner batched GMRES(8) to 1e-5).  Every
+    solution's true residual, recomputed by one oracle application of the full
+    D, meets 1e-10, and agrees with the library's own report."""
+    from paper_2407_08092_gb300 import lqdd
+    specs = [((24, 24, 24, 48), 1103), ((8, 8, 8, 8), 1101), ((16, 16, 16, 16), 1102), ((16, 16, 16, 32), 1104)]
+    n = 12
+    pairs = [Pair(L, eps=0.25, seed=seed, m0=0.05, csw=1.0) for L, seed in specs]
+    torch = pairs[0].torch
+    grp = lqdd.lq_group_create([p.ctx for p in pairs], torch.cuda.current_stream().cuda_stream)
+    try:
+        db, xs = [], []
+        for p in pairs:
+            b = torch.zeros((n, p.V, 4, 3), dtype=torch.complex128, device="cuda")
+            for r in range(n):
+                b[r, 0, r % 4, r // 4] = 1.0
+            db.append(b)
+            xs.append(torch.zeros_like(b))
+        status, stats = lqdd.lq_solve_group(grp, pairs[0].ctx, lqdd.make_batch_params(), db, xs)
+        assert status == lqdd.LQ_OK, lqdd.lq_status_string(status)
+        k = 0
+        worst = 0.0
+        for p, b, x in zip(pairs, db, xs):
+            bh, xh = p.host(b), p.host(x)
+            for r in range(n):
+                r_true = np.linalg.norm(bh[r] - p.lat.dirac(xh[r])) / np.linalg.norm(bh[r])
+                assert r_true <= 1e-10, (p.L, r, r_true)
+                assert abs(r_true - stats[k].rel_resid_true) <= 1e-3 * r_true + 1e-15
+                worst = max(worst, r_true)
+                k += 1
+        assert k == 4 * n and worst > 0
+    finally:
+        lqdd.lq_group_destroy(grp)
+        for p in pairs:
+            p.close()

@@ -71,7 +71,7 @@ def test_fgmres_with_bf16_richardson_reaches_1e10():
         status, st = lqdd.lq_solve(p.ctx, prm, db, x)
         assert status == lqdd.LQ_OK
         r_true = np.linalg.norm(b - p.lat.dirac(p.host(x))) / np.linalg.norm(b)
-        assert r_true <= 2e-10
+        assert r_true <= 1e-10
     finally:
         p.close()
 

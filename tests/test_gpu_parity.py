@@ -109,27 +109,32 @@ def test_richardson_smoother(pair, lqdd, prec):
         e = pair.torch.empty((lat.V, 4, 3), dtype=pair.torch.complex128, device="cuda")
         lqdd.lq_smooth(pair.ctx, p, pair.dev(r), e)
         ref = oracle.smoother(lat, r, "richardson", n, omega=omega)
-        assert rel(pair.host(e), ref) < TOL[prec] * (2 if prec == 1 else 1)
+        assert rel(pair.host(e), ref) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "df64"])
 def test_gmres_smoother(pair, lqdd, prec):
     """M r with GMRES(n, m) from zero on D_S (Algorithm 2): the iterate of a
     fixed number of cycles is the unique residual minimiser of each cycle, so
-    it agrees up to rounding amplified by the Krylov basis conditioning."""
+    it agrees up to rounding amplified by the Krylov basis conditioning.  With
+    two cycles of four steps that amplification is small: measured on GB300 the
+    FP32 smoother is within 1.2e-7 of the oracle on every shape here (an FP32
+    D_S apply errs by 1e-7), so the workload's FP32 and FP64 bounds hold."""
     lat = pair.lat
     r = synth.gaussian_spinor(lat.V, 7000 + lat.V)
     p = lqdd.make_params(smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=2, smooth_m=4, inner_prec=prec)
     e = pair.torch.empty((lat.V, 4, 3), dtype=pair.torch.complex128, device="cuda")
     lqdd.lq_smooth(pair.ctx, p, pair.dev(r), e)
     ref = oracle.smoother(lat, r, "gmres", 2, m=4)
-    assert rel(pair.host(e), ref) < (1e-4 if prec == 1 else 1e-10)
+    assert rel(pair.host(e), ref) < TOL[prec]
 
 
 def _check_solution(pair, b, x, tol):
+    """The true residual of the GPU solution, recomputed by the oracle on the
+    full lattice, meets the solve's tolerance."""
     lat = pair.lat
     r_true = np.linalg.norm(b - lat.dirac(x)) / np.linalg.norm(b)
-    assert r_true <= tol * 1.05, r_true
+    assert r_true <= tol, r_true
     return r_true
 
 
@@ -137,8 +142,6 @@ def _check_solution(pair, b, x, tol):
                                   "fgmres_df64_gmres32"])
 def test_solve(pair, lqdd, kind):
     lat = pair.lat
-    if lat.V > 8 ** 4 and kind not in ("fgmres_gmres32", "fgmres_df64_gmres32"):
-        pytest.skip("large shape covered by the mixed solve")
     b = synth.gaussian_spinor(lat.V, 8000 + lat.V)
     db = pair.dev(b)
     x = pair.torch.zeros_like(db)
@@ -163,8 +166,8 @@ def test_solve(pair, lqdd, kind):
                              inner_prec=1)
     status, st = lqdd.lq_solve(pair.ctx, p, db, x)
     assert status == lqdd.LQ_OK, (lqdd.lq_status_string(status), st.as_dict())
-    assert st.rel_resid <= 1e-10 and st.rel_resid_true <= 2e-10
-    r_true = _check_solution(pair, b, pair.host(x), 2e-10)
+    assert st.rel_resid <= 1e-10 and st.rel_resid_true <= 1e-10
+    r_true = _check_solution(pair, b, pair.host(x), 1e-10)
     assert abs(r_true - st.rel_resid_true) <= 1e-3 * r_true + 1e-15
 
 
@@ -181,6 +184,67 @@ def test_solve_matches_oracle_solution(lqdd):
         assert rel(p.host(x), xo) < 1e-9
     finally:
         p.close()
+
+
+@pytest.fixture(scope="module")
+def c0_reference():
+    """The 8^4 workload (eps 0.25, m0 0.05, c_sw 1, link seed 1000, Gaussian
+    source seed 2000) with the oracle's solution to 1e-13 and an estimate of
+    ||D^{-1}||_2: power iteration on (D^+ D)^{-1} = D^{-1} D^{-+}, each step two
+    oracle solves (D^{-+} v = g5 D^{-1} g5 v), which approaches ||D^{-1}|| from
+    below."""
+    L = (8, 8, 8, 8)
+    p = Pair(L, eps=0.25, seed=1000, m0=0.05, csw=1.0)
+    lat = p.lat
+    b = synth.gaussian_spinor(lat.V, 2000)
+    x_orc, info = oracle.solve(lat, b, tol=1e-13, restart=30, max_restarts=400)
+    assert info["converged"]
+
+    def solve(v):
+        return oracle.solve(lat, v, tol=1e-6, restart=30, max_restarts=400)[0]
+
+    def solve_dag(v):
+        return lat.g5(solve(lat.g5(v)))
+
+    inv_norm = oracle.power_norm(solve, solve_dag, synth.gaussian_spinor(lat.V, 5), 6)
+    yield p, b, x_orc, info["rel_resid_true"], inv_norm
+    p.close()
+
+
+@pytest.mark.parametrize("kind", ["df64_gmres32", "df64_rich_bf16", "df64_sap32", "f64_gmres30"])
+def test_solution_error_against_oracle_8x4(lqdd, c0_reference, kind):
+    """The solution of the mixed-precision solves (FP64-class outer FGMRES, FP32 or
+    BF16 inner smoother) against the oracle's FP64 solution on 8^4.  The bound is
+    the one the tolerance implies: x - x_orc = D^{-1}(r_orc - r), so
+    ||x - x_orc|| <= ||D^{-1}|| (||r|| + ||r_orc||), with ||D^{-1}|| taken as twice
+    the oracle's power-iteration estimate (which converges from below)."""
+    p, b, x_orc, rres_orc, inv_norm = c0_reference
+    lat = p.lat
+    norm = lqdd.lq_estimate_norm(p.ctx, 0, 20, p.dev(b[:lat.Vh]))
+    common = dict(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10, max_restarts=50)
+    if kind == "df64_gmres32":
+        prm = lqdd.make_params(**common, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
+                               smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+    elif kind == "df64_rich_bf16":
+        prm = lqdd.make_params(**common, smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=0.8 / norm,
+                               inner_prec=lqdd.LQ_BF16)
+    elif kind == "df64_sap32":
+        prm = lqdd.make_params(**common, smoother=lqdd.LQ_SMOOTH_SAP, smooth_n=3, smooth_m=4,
+                               inner_prec=lqdd.LQ_F32)
+    else:
+        prm = lqdd.make_params(tol=1e-10, restart=30, max_restarts=400)
+    db = p.dev(b)
+    x = p.torch.zeros_like(db)
+    status, st = lqdd.lq_solve(p.ctx, prm, db, x)
+    assert status == lqdd.LQ_OK, (lqdd.lq_status_string(status), st.as_dict())
+    xg = p.host(x)
+    r = np.linalg.norm(b - lat.dirac(xg))
+    nb = np.linalg.norm(b)
+    assert r <= 1e-10 * nb
+    err = rel(xg, x_orc)
+    bound = 2.0 * inv_norm * (r + rres_orc * nb) / np.linalg.norm(x_orc)
+    assert err <= bound, (kind, err, bound, inv_norm)
+    assert bound < 1e-8          # the bound itself is tight enough to mean something
 
 
 def test_deterministic(lqdd):
