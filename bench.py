@@ -15,8 +15,17 @@ a_k ~ N(0,1) (seed 1001), c_sw = 1.0, m0 = 0.02, Gaussian complex source
 
 value = algorithmic bytes of every library kernel in the timed steps (the
 library counts them per launch) / device time of the steps, in GB/s, summed
-over ranks.  The plain FP64 GMRES(30) solve of the same system (native FP64
-and df64) is timed beside it for the mixed-vs-FP64 half of the metric.
+over ranks.  Beside it, as named fields of the same line:
+
+  ds_f32   the FP32 D_S (K1 + K2) on 32^3 x 64, 48^3 x 96 and 8^4 against the
+           measured HBM bandwidth (the operator half of the metric);
+  solve    the mixed solve against plain FP64 GMRES(30) to 1e-10 on the same
+           lattices: times, speed-up, true residuals, and the relative
+           difference of the two solutions;
+  batched, force, sap, bf16   the other workloads, summarised.
+
+--detail PATH writes the per-kernel-class profile and every section's full
+record to a JSON file.
 
 --impl reference runs the FP64 CPU oracle instead (the test oracle, as it
 stands) on the host cores: each step applies the oracle's D_S (Eq. 3) to a
@@ -60,6 +69,9 @@ def parse():
     ap.add_argument("--no-sap", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-48x96", action="store_true")
+    ap.add_argument("--no-8x4", action="store_true")
+    ap.add_argument("--detail", default=None,
+                    help="write the per-kernel-class profile and every section's full record to this JSON file")
     return ap.parse_args()
 
 
@@ -161,6 +173,49 @@ def oracle_ds_sample(seconds: float, min_apps: int = 3):
     return gbs, n, dt, oracle.threads()
 
 
+def oracle_c0_solves():
+    """The oracle's odd-even solves of the 8^4 workload (eps 0.25, m0 0.05, c_sw 1,
+    link seed 1000, Gaussian source seed 2000) to 1e-10 on the host cores: plain
+    GMRES(30) and FGMRES(30) right-preconditioned by Richardson(5, delta 0.8),
+    omega from 30 power iterations (not timed)."""
+    import numpy as np
+
+    import oracle
+    from paper_2407_08092_gb300 import synth
+    L = (8, 8, 8, 8)
+    lat = oracle.Lattice(L, synth.gauge_links(L, EPS, 1000), m0=0.05, csw=CSW, t_bc=TBC)
+    _ = lat.C, lat.Cinv
+    b = synth.gaussian_spinor(lat.V, 2000)
+    norm = oracle.power_norm(lat.schur, lat.schur_dag, b[:lat.Vh], 30)
+    out = {}
+    for name, kw in (("gmres30", {"solver": "gmres", "restart": 30}),
+                     ("fgmres30_rich5", {"solver": "fgmres", "restart": 30, "precond": "richardson",
+                                         "smooth_n": 5, "omega": 0.8 / norm})):
+        t0 = time.perf_counter()
+        _, info = oracle.solve(lat, b, tol=1e-10, max_restarts=200, **kw)
+        out[name] = {"s": round(time.perf_counter() - t0, 3), "iters": info["iters"],
+                     "rres": float(f"{info['rel_resid_true']:.3g}")}
+    del np
+    return out
+
+
+def cpu_baseline(seconds: float):
+    """The oracle as it stands on the host cores: its D_S on the 16^3 x 32 sample
+    with every core and with one core, and its two 8^4 solves with every core."""
+    import oracle
+    g, n, dt, cores = oracle_ds_sample(seconds)
+    oracle.set_threads(1)
+    try:
+        g1, n1, dt1, _ = oracle_ds_sample(max(2.0, seconds / 4))
+    finally:
+        oracle.set_threads(cores)
+    c0 = oracle_c0_solves()
+    return {"value": round(g, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle FP64 D_S x{n} ({dt:.0f} s; 1 core: x{n1}, {dt1:.0f} s) on 16^3x32 with this "
+                      f"workload's parameters, FP64 D_S bytes; c0: its 8^4 solves to 1e-10",
+            "single_core": {"value": round(g1, 3), "cores": 1}, "c0": c0}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -194,10 +249,33 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def traffic_per_launch(cls_name: str, V: int):
     """DRAM bytes per launch of a kernel class from the committed ncu summary
-    (bytes per unit site, the unit being a lattice site `V` or a site of one
-    parity `Vh`), or None when the kernel's source file changed since the
-    capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    (profiles/traffic.txt), or None when the kernel's source file changed since
+    the capture."""
+    return table_per_launch("traffic.txt", cls_name, V)
+
+
+# Kernel classes whose roof is arithmetic, not HBM: native FP64 runs on the
+# FP64 pipe (GB300: 2 FMA/clk/SM -> 152 * 2 * 2 flop * 2.07 GHz = 1.26 TFLOP/s,
+# the nominal 1.25 TFLOP/s), df64 on the FP32 pipe.  A df64 class is judged by
+# instruction issue: the warp instructions one launch executes (ncu
+# sm__inst_executed.sum per unit site, profiles/issue.txt) over its duration,
+# against the SMs' issue ceiling of 152 SMs x 4 schedulers x 1 warp instruction
+# per clock at 2.07 GHz = 1258.6 G warp instructions/s.  Beside it stays the
+# flop model: 15 FP32 instructions per df64 FMA (2prod 2, cross terms 2, 2sum
+# 6, low-part adds 2, fast2sum 3): 152 * 128 lanes * 2.07 GHz / 15 * 2 flop =
+# 5.37 TFLOP/s FP64-equivalent.
+ALU_F64 = {"hop_k1_f64", "hop_k2_f64"}
+ALU_DF64 = {"hop_k1_df64", "hop_k2_df64", "hop_other", "clover", "clover_field", "force"}
+SM_MHZ_MAX = 2070.0
+ISSUE_PEAK_G = 152 * 4 * SM_MHZ_MAX / 1e3   # G warp instructions per second
+
+
+def table_per_launch(fname: str, cls_name: str, V: int):
+    """Per-launch value of a kernel class from a committed ncu table
+    (profiles/<fname>: class, value per unit site, unit V or Vh, source file,
+    sha256[:16] of that file at capture), or None when the kernel's source file
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         for ln in open(path):
             parts = ln.split()
@@ -211,23 +289,24 @@ def traffic_per_launch(cls_name: str, V: int):
     return None
 
 
-# Kernel classes whose roof is arithmetic, not HBM: native FP64 runs on the
-# FP64 pipe (GB300: 2 FMA/clk/SM -> 152 * 2 * 2 flop * 2.07 GHz = 1.26 TFLOP/s,
-# the nominal 1.25 TFLOP/s), df64 on the FP32 pipe at 15 FP32 instructions per
-# df64 FMA (2prod 2, cross terms 2, 2sum 6, low-part adds 2, fast2sum 3):
-# 152 * 128 lanes * 2.07 GHz / 15 * 2 flop = 5.37 TFLOP/s FP64-equivalent.
-ALU_F64 = {"hop_k1_f64", "hop_k2_f64"}
-ALU_DF64 = {"hop_k1_df64", "hop_k2_df64", "hop_other", "clover", "clover_field", "force"}
-SM_MHZ_MAX = 2070.0
-
-
 def roofline_of(name, d, pk, V):
     t = d["ms"] / 1e3
     base = {"kernel": name, "avg_launch_us": round(1e3 * d["ms"] / d["launches"], 2),
             "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
             "algorithmic_flops_per_launch": d["flops"] / d["launches"],
             "gbs": round(d["bytes"] / t / 1e9, 1), "hbm_frac": round(d["bytes"] / t / 1e9 / pk["hbm_gbs"], 4)}
-    if name in ALU_F64 or name in ALU_DF64:
+    inst = table_per_launch("issue.txt", name, V) if name in ALU_DF64 else None
+    if inst is not None:
+        # instructions per launch over the launch's average duration, against the issue ceiling
+        ach = inst / (d["ms"] / d["launches"] / 1e3) / 1e9
+        model = d["flops"] / t / 1e12 / (152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2 / 1e12)
+        base.update({"bound": "issue", "achieved": round(ach, 1), "peak": round(ISSUE_PEAK_G, 1),
+                     "unit": "Gwarp-inst/s", "frac": round(ach / ISSUE_PEAK_G, 4),
+                     "traffic": traffic_per_launch(name, V),
+                     "peak_src": f"hardware issue ceiling: 152 SMs x 4 schedulers x {SM_MHZ_MAX:.0f} MHz; "
+                                 "instructions from ncu sm__inst_executed.sum (profiles/issue.txt)",
+                     "df64_model_frac": round(model, 4)})
+    elif name in ALU_F64 or name in ALU_DF64:
         peak = (152 * 2 * 2 * SM_MHZ_MAX * 1e6 if name in ALU_F64 else 152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2) / 1e12
         ach = d["flops"] / t / 1e12
         base.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
@@ -298,6 +377,7 @@ def run_batched(lqdd, synth, torch, stream, dev):
             return worst, ok
 
         res = {}
+        x_group = None
         for name, reps in (("group", 3), ("per_lattice", 3), ("sequential", 2), ("fp64_sequential", 1)):
             run(name)                                   # warm-up: workspace, tuning, graph capture
             times = []
@@ -310,8 +390,14 @@ def run_batched(lqdd, synth, torch, stream, dev):
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(z))
             res[name] = {"ms": round(sorted(times)[len(times) // 2], 2), "worst_rel_resid_true": worst, "status": ok}
+            if name == "group":
+                x_group = [x.clone() for x in xs]
+        # the group's solutions against the plain FP64 ones (left in xs by the last run)
+        res["xdiff_vs_fp64"] = max(max(rel_diff(torch, xg[r], xf[r]) for r in range(n))
+                                   for xg, xf in zip(x_group, xs))
         spt, rpt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
-        res["tuning"] = {"sites_per_tile": spt, "rhs_per_thread": rpt, "rhs_per_tile": rpt * 128 // spt,
+        res["tuning"] = {"sites_per_tile": spt, "rhs_per_thread": rpt,
+                         "rhs_per_tile": rpt * 128 // spt if rpt else "all (staged links and clover)",
                          "grid": grid, "blas_blocks": blas, "hop_pair_ms": round(hop_ms, 4),
                          "blas_pair_ms": round(blas_ms, 4)}
         res["speedup_vs_per_lattice"] = round(res["per_lattice"]["ms"] / res["group"]["ms"], 2)
@@ -370,11 +456,75 @@ def run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks, V, omega):
     return res
 
 
+def ds_rate(lqdd, ctx, prec, xe, ye, pk, reps=10):
+    """D_S = K1 + K2 in precision prec: device time of the two hopping kernels per
+    apply (CUDA events around each launch), algorithmic GB/s and fraction of the
+    measured HBM bandwidth."""
+    name = {lqdd.LQ_F32: "f32", lqdd.LQ_F64: "f64", lqdd.LQ_DF64: "df64", lqdd.LQ_BF16: "bf16"}[prec]
+    lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
+    lqdd.lq_profile(ctx, 1)
+    for _ in range(reps):
+        lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
+    prof = read_profile(lqdd, ctx)
+    lqdd.lq_profile(ctx, 0)
+    k1, k2 = f"hop_k1_{name}", f"hop_k2_{name}"
+    ms = (prof[k1]["ms"] + prof[k2]["ms"]) / reps
+    by = (prof[k1]["bytes"] + prof[k2]["bytes"]) / reps
+    gbs = by / (ms / 1e3) / 1e9
+    return {"us": round(1e3 * ms, 1), "gbs": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+
+
+def timed_solves(lqdd, torch, stream, ctx, b, cases):
+    """Each (name, params, reps) solve from zero: the median device time, its
+    stats, and the solution of the last run."""
+    res, xs = {}, {}
+    x = torch.zeros_like(b)
+    for name, prm, reps in cases:
+        x.zero_()
+        lqdd.lq_solve(ctx, prm, b, x)                 # workspace
+        runs = []
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            status, st = lqdd.lq_solve(ctx, prm, b, x)
+            z.record(stream)
+            torch.cuda.synchronize()
+            runs.append((a.elapsed_time(z), st.as_dict(), lqdd.lq_status_string(status)))
+        ms, st, status = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+        res[name] = {"ms": round(ms, 2), "status": status, **st}
+        xs[name] = x.clone()
+    return res, xs
+
+
+def rel_diff(torch, a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def mixed_params(lqdd):
+    """The mixed-precision solve: FGMRES(10) in df64 right-preconditioned by
+    GMRES(8) in FP32 to 1e-5, to a 1e-10 relative residual of D x = b."""
+    return lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
+                            max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
+                            smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+
+
+def solve_summary(res, xs, torch, keys=("mixed", "fp64")):
+    """Compact record of a mixed-vs-FP64 comparison: times, ratio, true residuals
+    and the relative difference of the two solutions."""
+    m, f = keys
+    return {"mixed_ms": res[m]["ms"], "fp64_ms": res[f]["ms"], "x": round(res[f]["ms"] / res[m]["ms"], 2),
+            "rres": [float(f"{res[m]['rel_resid_true']:.3g}"), float(f"{res[f]['rel_resid_true']:.3g}")],
+            "xdiff": float(f"{rel_diff(torch, xs[m], xs[f]):.3g}"),
+            "ok": res[m]["status"] == "LQ_OK" and res[f]["status"] == "LQ_OK"}
+
+
 def run_48x96(lqdd, synth, torch, stream, dev, pk):
     """The 48^3 x 96 workload (eps 0.2, m0 0.01, c_sw 1, antiperiodic t, link
-    seed 1002, Gaussian source seed 2002): the FP32 D_S apply against the
+    seed 1002, Gaussian source seed 2002): the FP32 and FP64 D_S against the
     measured HBM bandwidth, and the mixed solve against plain FP64 GMRES(30),
-    both to 1e-10 on the true residual."""
+    both to 1e-10, with the relative difference of their solutions."""
     import numpy as np
     L = (48, 48, 48, 96)
     V = int(np.prod(L))
@@ -384,41 +534,43 @@ def run_48x96(lqdd, synth, torch, stream, dev, pk):
         b = torch.from_numpy(synth.gaussian_spinor(V, 2002)).to(dev)
         xe = b[:V // 2].contiguous()
         ye = torch.empty_like(xe)
-        res = {"lattice": list(L)}
-        for prec, name in ((lqdd.LQ_F32, "f32"), (lqdd.LQ_F64, "f64")):
-            lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
-            lqdd.lq_profile(ctx, 1)
-            for _ in range(10):
-                lqdd.lq_apply(ctx, lqdd.LQ_OP_SCHUR, prec, xe, ye)
-            prof = read_profile(lqdd, ctx)
-            lqdd.lq_profile(ctx, 0)
-            k1, k2 = f"hop_k1_{name}", f"hop_k2_{name}"
-            ms = (prof[k1]["ms"] + prof[k2]["ms"]) / 10
-            by = (prof[k1]["bytes"] + prof[k2]["bytes"]) / 10
-            res[f"ds_{name}"] = {"us": round(1e3 * ms, 1), "gbs": round(by / (ms / 1e3) / 1e9, 1),
-                                 "hbm_frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
-        x = torch.zeros_like(b)
-        mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                                 max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
-                                 smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+        res = {"lattice": list(L), "ds_f32": ds_rate(lqdd, ctx, lqdd.LQ_F32, xe, ye, pk),
+               "ds_f64": ds_rate(lqdd, ctx, lqdd.LQ_F64, xe, ye, pk)}
         fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
-        for name, prm, reps in (("mixed", mixed, 3), ("fp64", fp64, 1)):
-            x.zero_()
-            lqdd.lq_solve(ctx, prm, b, x)
-            ts = []
-            for _ in range(reps):
-                x.zero_()
-                torch.cuda.synchronize()
-                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                status, st = lqdd.lq_solve(ctx, prm, b, x)
-                z.record(stream)
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(z))
-            res[f"{name}_ms"] = round(sorted(ts)[len(ts) // 2], 2)
-            res[name] = {"iters": st.iters, "inner_iters": st.inner_iters, "rel_resid_true": st.rel_resid_true,
-                         "status": lqdd.lq_status_string(status)}
-        res["speedup"] = round(res["fp64_ms"] / res["mixed_ms"], 2)
+        sol, xs = timed_solves(lqdd, torch, stream, ctx, b, (("mixed", mixed_params(lqdd), 3), ("fp64", fp64, 1)))
+        res["solves"] = sol
+        res["solve"] = solve_summary(sol, xs, torch)
+        return res
+    finally:
+        lqdd.lq_destroy(ctx)
+
+
+def run_c0(lqdd, synth, torch, stream, dev, pk):
+    """The 8^4 workload (eps 0.25, m0 0.05, c_sw 1, link seed 1000, Gaussian
+    source seed 2000): the D_S apply (its 4 MB working set sits in L2, so its
+    GB/s is no HBM figure), plain FP64 GMRES(30), FGMRES(30) in FP64 with
+    Richardson(5, delta 0.8) in FP32, and the mixed solve, all to 1e-10."""
+    import numpy as np
+    L = (8, 8, 8, 8)
+    V = int(np.prod(L))
+    ctx = lqdd.lq_create(lqdd.make_lattice(L, TBC, 0.05, CSW), stream.cuda_stream)
+    try:
+        lqdd.lq_set_gauge(ctx, torch.from_numpy(synth.gauge_links(L, EPS, 1000)).to(dev))
+        b = torch.from_numpy(synth.gaussian_spinor(V, 2000)).to(dev)
+        xe = b[:V // 2].contiguous()
+        ye = torch.empty_like(xe)
+        res = {"lattice": list(L), "ds_f32": ds_rate(lqdd, ctx, lqdd.LQ_F32, xe, ye, pk, reps=50),
+               "ds_f64": ds_rate(lqdd, ctx, lqdd.LQ_F64, xe, ye, pk, reps=50)}
+        norm = lqdd.lq_estimate_norm(ctx, lqdd.LQ_F64, 30, xe)
+        fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
+        rich = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, tol=1e-10, restart=30, max_restarts=100,
+                                smoother=lqdd.LQ_SMOOTH_RICHARDSON, smooth_n=5, omega=0.8 / norm,
+                                inner_prec=lqdd.LQ_F32)
+        sol, xs = timed_solves(lqdd, torch, stream, ctx, b, (("mixed", mixed_params(lqdd), 5), ("fp64", fp64, 5),
+                                                              ("fgmres_rich5", rich, 5)))
+        res["solves"] = sol
+        res["solve"] = solve_summary(sol, xs, torch)
+        res["solve"]["fgmres_rich5_ms"] = sol["fgmres_rich5"]["ms"]
         return res
     finally:
         lqdd.lq_destroy(ctx)
@@ -571,9 +723,7 @@ def run_ours(args):
     dbe = db[:Vh].contiguous()
     x = torch.zeros_like(db)
     e = torch.empty_like(db)
-    mixed = lqdd.make_params(solver=lqdd.LQ_SOLVER_FGMRES, prec=lqdd.LQ_DF64, tol=1e-10, restart=10,
-                             max_restarts=20, smoother=lqdd.LQ_SMOOTH_GMRES, smooth_n=40, smooth_m=8,
-                             smooth_tol=1e-5, inner_prec=lqdd.LQ_F32)
+    mixed = mixed_params(lqdd)
     info = {}
 
     def step(Ud, bd, bed, xd, ed):
@@ -618,38 +768,31 @@ def run_ours(args):
     clk = clocks.stop()
     step_bytes = (b1 - b0) / args.steps
 
-    # the plain FP64 GMRES(30) solve of the same system, timed beside the mixed one
+    # the operator the metric names: FP32 D_S on this lattice against measured HBM
+    pk = peaks()
+    ds_c1 = ds_rate(lqdd, ctx, lqdd.LQ_F32, dbe, torch.empty_like(dbe), pk, reps=20)
+
+    # the plain FP64 GMRES(30) solve of the same system (native FP64 and df64),
+    # timed beside the mixed one, medians of 5
     fp64 = lqdd.make_params(tol=1e-10, restart=30, max_restarts=200)
     df64 = lqdd.make_params(prec=lqdd.LQ_DF64, tol=1e-10, restart=30, max_restarts=200)
-    x.zero_()
-    lqdd.lq_solve(ctx, fp64, db, x)            # allocate the FP64 workspace
-    x.zero_()
-    lqdd.lq_solve(ctx, df64, db, x)            # and the df64 one
-    times = {}
-    for name, prm in (("fp64", fp64), ("df64", df64), ("mixed", mixed)):
-        runs = []
-        for _ in range(5):
-            x.zero_()
-            torch.cuda.synchronize()
-            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            status, st = lqdd.lq_solve(ctx, prm, db, x)
-            z.record(stream)
-            torch.cuda.synchronize()
-            runs.append((a.elapsed_time(z), st.as_dict(), lqdd.lq_status_string(status)))
-        times[name] = sorted(runs, key=lambda r: r[0])[2]          # median of 5
+    solves, xsol = timed_solves(lqdd, torch, stream, ctx, db, (("fp64", fp64, 5), ("df64", df64, 5),
+                                                              ("mixed", mixed, 5)))
+    solve_c1 = solve_summary(solves, xsol, torch)
+    solve_c1["df64_ms"] = solves["df64"]["ms"]
+    del xsol
 
     # smoothers on the benchmark lattice: one SAP(3, 4) call (the paper's Table 2
     # smoother call; 4^4 blocks, FP32) against one odd-even Richardson(5) call,
     # and the FGMRES solve preconditioned by SAP(3, 4) against the mixed solve
     sap = None
     if not args.no_sap:
-        sap = run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks=peaks(), V=V, omega=info["omega"])
+        sap = run_sap(lqdd, torch, stream, ctx, db, x, pk_peaks=pk, V=V, omega=info["omega"])
 
     # BF16 storage of spinors and links against FP32
     bf16 = None
     if not args.no_bf16:
-        bf16 = run_bf16(lqdd, torch, stream, ctx, db, x, peaks(), V, info["omega"])
+        bf16 = run_bf16(lqdd, torch, stream, ctx, db, x, pk, V, info["omega"])
 
     # batched: 12 spin-colour point sources on each of four lattices
     batched = None
@@ -658,11 +801,15 @@ def run_ours(args):
 
     big = None
     if not args.no_48x96 and world == 1:
-        big = run_48x96(lqdd, synth, torch, stream, dev, peaks())
+        big = run_48x96(lqdd, synth, torch, stream, dev, pk)
+
+    c0 = None
+    if not args.no_8x4 and world == 1:
+        c0 = run_c0(lqdd, synth, torch, stream, dev, pk)
 
     force = None
     if not args.no_force:
-        force = run_force(lqdd, synth, torch, stream, dev, peaks())
+        force = run_force(lqdd, synth, torch, stream, dev, pk)
 
     # e2e: host (pinned) inputs and result, copies inside the timed region.  The
     # inputs are double-buffered: a copy stream uploads step i+1's gauge field
@@ -723,53 +870,70 @@ def run_ours(args):
         return 0
 
     value = tot_bytes / (ms / 1e3) / 1e9
-    pk = peaks()
     # dominant kernel class by device time
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
     roofline = None
     if dom:
-        roofline = roofline_of(dom[0], dom[1], pk, V)
+        r = roofline_of(dom[0], dom[1], pk, V)
+        roofline = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                      "avg_launch_us", "algorithmic_bytes_per_launch")}
         roofline["share_of_step"] = round(dom[1]["ms"] / ms, 4)
+        roofline["peak_src"] = "measured"
     ops = {k: roofline_of(k, prof[k], pk, V) for k in sorted(prof) if prof[k]["ms"] > 0 and prof[k]["launches"]}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        g, n, dt, cores = oracle_ds_sample(args.cpu_seconds)
-        cpu = {"value": round(g, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle D_S (Eq. 3) x{n} on a 16^3x32 lattice with this workload's parameters "
-                         f"({dt:.1f} s); GB/s by the same algorithmic byte count as the FP64 D_S kernels"}
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    def pick(d, *keys):
+        return None if d is None else {k: d[k] for k in keys if k in d}
+
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
-        "config": {"workload": "32^3x64 odd-even Wilson-clover step: set_gauge + 10 FP32 power iterations + "
-                               "Richardson(5) FP32 smoother + FGMRES(10) df64 / GMRES(8) FP32 solve to 1e-10",
-                   "lattice": list(L_WORK), "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC,
-                   "l2": "inputs larger than L2 (gauge field 1.2 GB, each spinor field 0.4 GB); no flush",
+        "config": {"workload": "32^3x64 step: set_gauge, 10 FP32 power its, Richardson(5) FP32, "
+                               "FGMRES(10) df64 / GMRES(8) FP32 to 1e-10",
+                   "eps": EPS, "m0": M0, "csw": CSW, "t_bc": TBC,
+                   "l2": "inputs larger than L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": None if e2e is None else {
             "value": round(e2e["step_bytes"] * world / (e2e["ms_per_step"] / 1e3) / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
-            "ms_per_step": round(e2e["ms_per_step"], 3), "overlap": e2e["overlap"]},
+            "ms_per_step": round(e2e["ms_per_step"], 3)},
         "gpu_launches": int(n1 - n0),
         "clocks": clk,
-        "op": ops,
-        "solve": {"mixed_ms": round(times["mixed"][0], 2), "fp64_ms": round(times["fp64"][0], 2),
-                  "df64_ms": round(times["df64"][0], 2),
-                  "speedup": round(times["fp64"][0] / times["mixed"][0], 2),
-                  "speedup_vs_df64": round(times["df64"][0] / times["mixed"][0], 2),
-                  "mixed": times["mixed"][1], "fp64": times["fp64"][1], "df64": times["df64"][1],
-                  "status": {k: times[k][2] for k in times}},
-        "batched": batched,
-        "force": force,
-        "sap": sap,
-        "bf16": bf16,
-        "lattice_48x96": big,
-        "kernels": prof,
-        "step_bytes": step_bytes,
+        # the metric's two halves, named: FP32 D_S against measured HBM, and the
+        # mixed solve against plain FP64 GMRES(30) (x = speed-up, rres = true
+        # residuals, xdiff = ||x_mixed - x_fp64|| / ||x_fp64||)
+        "ds_f32": {"32^3x64": ds_c1, "48^3x96": None if big is None else big["ds_f32"],
+                   "8^4_in_L2": None if c0 is None else c0["ds_f32"]},
+        "solve": {"32^3x64": solve_c1, "48^3x96": None if big is None else big["solve"],
+                  "8^4": None if c0 is None else c0["solve"]},
+        "batched": None if batched is None else {
+            "group_ms": batched["group"]["ms"], "per_lattice_ms": batched["per_lattice"]["ms"],
+            "seq_mixed_ms": batched["sequential"]["ms"], "seq_fp64_ms": batched["fp64_sequential"]["ms"],
+            "x_fp64": batched["speedup_vs_fp64"], "worst_rres": float(f"{batched['group']['worst_rel_resid_true']:.3g}"),
+            "xdiff": float(f"{batched['xdiff_vs_fp64']:.3g}"),
+            "hop_pair_ms": batched["tuning"]["hop_pair_ms"]},
+        "force": None if force is None else {
+            "ms": force["fermion_force_ms"], "kernel_ms": force["force_call_ms"],
+            "frac": (force.get("roofline") or {}).get("frac")},
+        "sap": None if sap is None else {
+            "sap34_ms": sap["sap_3_4_ms"], "rich5_ms": sap["richardson_5_ms"], "fgmres_sap_ms": sap["fgmres_sap_ms"],
+            "frac": (sap.get("roofline") or {}).get("frac")},
+        "bf16": None if bf16 is None else pick(bf16["bf16"], "ds_us", "ds_frac", "rel_err_vs_fp64"),
+        "detail": args.detail,
     }
     print(json.dumps(line), flush=True)
+    if args.detail:
+        detail = {"line": line, "kernels": prof, "op": ops, "step_bytes": step_bytes,
+                  "solve_32x64": solves, "sap": sap, "bf16": bf16, "batched": batched, "lattice_48x96": big,
+                  "lattice_8x4": c0, "force": force, "e2e": e2e}
+        os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+        with open(args.detail, "w") as f:
+            json.dump(detail, f, indent=1, default=str)
     if dist:
         dist.destroy_process_group()
     return 0

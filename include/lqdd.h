@@ -57,7 +57,8 @@ typedef enum {
     LQ_ERR_NOT_CONVERGED = 4,  /* tolerance not reached within max_restarts; x is the last iterate */
     LQ_ERR_BREAKDOWN = 5,      /* a clover block is not invertible (non-positive LDL pivot) */
     LQ_ERR_NAN = 6,            /* a NaN or Inf appeared in a residual or norm */
-    LQ_ERR_STATE = 7           /* call out of order (e.g. an operator before lq_set_gauge) */
+    LQ_ERR_STATE = 7,          /* call out of order (e.g. an operator before lq_set_gauge) */
+    LQ_ERR_BOUNDS = 8          /* checked build only: a kernel's index check failed (lq_bounds_check) */
 } lq_status;
 
 /* LQ_BF16 stores spinors and 12-real links in BF16 (8 significand bits) and
@@ -244,15 +245,20 @@ lq_status lq_solve_group(lq_group *grp, const lq_solver_params *params, const in
 lq_status lq_group_set_autotune(lq_group *grp, int on);
 
 /* Pin the launch shape of the batched hop instead of autotuning it:
- * sites_per_tile 16, 32, 64 or 128, rhs_per_thread 1 or 2, grid_factor 1 or 2
- * (times the resident blocks, persistent) or 0 (one block per tile).  The BLAS
+ * sites_per_tile 16, 32, 64 or 128 with rhs_per_thread 1 or 2 (each thread one
+ * or two right-hand sides of one site), or sites_per_tile 32 or 64 with
+ * rhs_per_thread 0 (the staged form: a tile's links and clover blocks are read
+ * once into shared memory and applied to every right-hand side of its lattice);
+ * grid_factor 1 or 2 (times the resident blocks, persistent) or 0 (one block
+ * per tile).  The BLAS
  * blocking keeps its default.  Drops the current layout and captured graphs;
  * lq_group_set_autotune(grp, 1) returns to autotuning. */
 lq_status lq_group_set_shape(lq_group *grp, int sites_per_tile, int rhs_per_thread, int grid_factor);
 
 /* The launch shapes in use after a solve: sites per tile of the batched hop,
  * right-hand sides per thread (1 or 2; right-hand sides per tile =
- * rhs_per_thread * 128 / sites_per_tile), its grid, BLAS blocks per system,
+ * rhs_per_thread * 128 / sites_per_tile; 0 for the staged form, whose tiles
+ * cover every right-hand side), its grid, BLAS blocks per system,
  * and the measured times of the chosen hop pair and BLAS pair (0 if untuned).
  * LQ_ERR_STATE before the first solve.  Any pointer may be NULL. */
 lq_status lq_group_tuning(lq_group *grp, int *sites_per_tile, int *rhs_per_thread, int *grid, int *blas_blocks,
@@ -349,15 +355,36 @@ lq_status lq_counters(lq_ctx *ctx, long long *launches, double *bytes);
  *   stream: cudaStream_t (NULL: the legacy default stream)
  * The call only enqueues work and does not synchronise.  The first call on a
  * device looks up the scratch array's device address for that device (with it
- * current) and caches it; make that first call before any stream capture.
+ * current) and caches it.  With CUDA's lazy module loading (the default), that
+ * first call may also load the library's module on the device, which allocates
+ * the device's copy of the array and of the kernels' code: make the first call
+ * on each device at set-up, outside any fixed memory budget, and before any
+ * stream capture.  Later calls allocate nothing.
  * All calls share the one scratch array, which keeps the last call's partial
  * sums; each call writes every slot it reads, so nothing needs clearing, but
  * calls whose kernels overlap on the GPU (different streams, or different host
  * threads on one device) race on it and must be serialised by the caller.
  * Errors: LQ_ERR_ARG for a NULL pointer, n_sites < 0 or
  * n_sites > LQ_NORM2_NOALLOC_MAX_SITES (nothing is launched); LQ_ERR_CUDA if
- * the device, the scratch address or a launch fails. */
+ * the device, the scratch address or a launch fails, or if a launch error from
+ * earlier work is pending on the calling thread (nothing is launched then, and
+ * that error is left for its owner to read). */
 lq_status lq_norm2_noalloc(const void *v, long long n_sites, double *out, void *stream);
+
+/* The index checks of the checked build (no paper counterpart: a test aid).
+ * A library compiled with -DLQ_BOUNDS (LQ_NVCC_EXTRA, or build(checked=True),
+ * which writes liblqdd_checked.so) range-checks every computed neighbour,
+ * site, block-local and layout-tile index inside its kernels against the
+ * extent of the array it indexes.  A failed check does not trap: the kernel
+ * counts it, remembers the code of the first one (the enum BoundsSite of the
+ * internal header: 1 hop site, 2 hop neighbour, 3 df64 hop neighbour, 4
+ * batched-hop neighbour, 5 SAP block-local, 6 SAP lattice, 7 clover/force
+ * lexicographic, 8 layout) and uses index 0 instead, so the access stays in
+ * bounds.  This call synchronises the current device, reads and clears those
+ * flags and returns LQ_ERR_BOUNDS if any check failed since the last call,
+ * else LQ_OK.  *checked = 1 in a checked build, 0 otherwise (where nothing is
+ * checked and the call returns LQ_OK).  Any pointer may be NULL. */
+lq_status lq_bounds_check(int *checked, unsigned long long *violations, int *first_code);
 
 /* A static description of the last failure on this context ("" if none). */
 const char *lq_last_error(lq_ctx *ctx);

@@ -867,11 +867,12 @@ void group_release(lq_group *G)
 // one another)
 void group_tiles(lq_group *G, int spt, int per_thread = 1)
 {
-    const int rpt = per_thread * (kHopBlock / spt);   // right-hand sides per tile
+    // right-hand sides per tile; the staged form (per_thread 0) covers all of them
+    const int rpt = per_thread * (kHopBlock / spt);
     std::vector<int4> t;
     for (size_t l = 0; l < G->mem.size(); l++) {
         const long long sb = (G->mem[l]->g.Vh + spt - 1) / spt;
-        const int groups = (G->nrhs[l] + rpt - 1) / rpt;
+        const int groups = per_thread == 0 ? 1 : (G->nrhs[l] + rpt - 1) / rpt;
         for (long long b = 0; b < sb; b++)
             for (int q = 0; q < groups; q++) t.push_back(make_int4((int)l, (int)b, q * rpt, 0));
     }
@@ -892,7 +893,7 @@ int group_grid(lq_group *G, int factor)
     if (factor == 0) return G->ntiles;
     int sms = 0;
     ck(gctx(G), cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gctx(G)->device), "cudaDeviceGetAttribute");
-    const long long g = (long long)factor * hop_group_resident(G->tune.rpt) * sms;
+    const long long g = (long long)factor * hop_group_resident(G->tune.rpt, G->tune.spt) * sms;
     return (int)(g < G->ntiles ? g : G->ntiles);
 }
 
@@ -939,7 +940,8 @@ void group_setup(lq_group *G, const std::vector<int> &nrhs, int m)
         G->k1_flops += hop_flops(HOP_K1, (double)ml->g.Vh * nrhs[l]);
         G->k2_flops += hop_flops(HOP_K2, (double)ml->g.Vh * nrhs[l]);
         max_tiles += (ml->g.Vh + 15) / 16 * ((nrhs[l] + 7) / 8) + (ml->g.Vh + 127) / 128 * nrhs[l] +
-                     (ml->g.Vh + 63) / 64 * ((nrhs[l] + 1) / 2) + (ml->g.Vh + 31) / 32 * ((nrhs[l] + 3) / 4);
+                     (ml->g.Vh + 63) / 64 * ((nrhs[l] + 1) / 2) + (ml->g.Vh + 31) / 32 * ((nrhs[l] + 3) / 4) +
+                     (ml->g.Vh + 31) / 32;
     }
     G->N = N;
     G->m = m;
@@ -1044,8 +1046,9 @@ void group_tune(lq_group *G)
     };
     float best = 1e30f;
     int best_spt = 32, best_rpt = 1, best_factor = 2;
-    for (int rpt : {1, 2})
+    for (int rpt : {1, 2, 0})
         for (int spt : {32, 64, 16, 128}) {
+            if (rpt == 0 && spt != 32 && spt != 64) continue;   // staged form: 32 or 64 sites per tile
             group_tiles(G, spt, rpt);
             for (int factor : {1, 2, 0}) {
                 G->tune.grid = group_grid(G, factor);
@@ -1253,7 +1256,42 @@ lq_status guarded(lq_ctx *c, F &&f)
 // C ABI
 // =====================================================================================
 
+namespace lq {
+// readers of the index-check flags of every translation unit (checked build)
+static std::vector<unsigned (*)(unsigned *)> &bounds_readers()
+{
+    static std::vector<unsigned (*)(unsigned *)> v;
+    return v;
+}
+void bounds_register(unsigned (*read_clear)(unsigned *first)) { bounds_readers().push_back(read_clear); }
+}  // namespace lq
+
 extern "C" {
+
+lq_status lq_bounds_check(int *checked, unsigned long long *violations, int *first_code)
+{
+    unsigned long long total = 0;
+    int first = 0;
+#ifdef LQ_BOUNDS
+    if (checked) *checked = 1;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return LQ_ERR_CUDA;
+    }
+    for (auto fn : lq::bounds_readers()) {
+        unsigned f = 0;
+        const unsigned n = fn(&f);
+        if (n && !first) first = (int)f;
+        total += n;
+    }
+    if (cudaGetLastError() != cudaSuccess) return LQ_ERR_CUDA;
+#else
+    if (checked) *checked = 0;
+#endif
+    if (violations) *violations = total;
+    if (first_code) *first_code = first;
+    return total ? LQ_ERR_BOUNDS : LQ_OK;
+}
 
 const char *lq_status_string(lq_status s)
 {
@@ -1266,6 +1304,7 @@ const char *lq_status_string(lq_status s)
     case LQ_ERR_BREAKDOWN: return "LQ_ERR_BREAKDOWN";
     case LQ_ERR_NAN: return "LQ_ERR_NAN";
     case LQ_ERR_STATE: return "LQ_ERR_STATE";
+    case LQ_ERR_BOUNDS: return "LQ_ERR_BOUNDS";
     }
     return "LQ_ERR_UNKNOWN";
 }
@@ -1649,8 +1688,10 @@ lq_status lq_group_set_shape(lq_group *G, int sites_per_tile, int rhs_per_thread
     if (!G) return LQ_ERR_ARG;
     return guarded(gctx(G), [&] {
         const int spt = sites_per_tile;
-        if ((spt != 16 && spt != 32 && spt != 64 && spt != 128) || (rhs_per_thread != 1 && rhs_per_thread != 2) ||
-            grid_factor < 0 || grid_factor > 2)
+        const bool staged = rhs_per_thread == 0 && (spt == 32 || spt == 64);
+        const bool threads = (spt == 16 || spt == 32 || spt == 64 || spt == 128) &&
+                             (rhs_per_thread == 1 || rhs_per_thread == 2);
+        if (!(staged || threads) || grid_factor < 0 || grid_factor > 2)
             fail(gctx(G), LQ_ERR_ARG, "bad launch shape");
         G->autotune = false;
         G->pin_spt = spt;

@@ -79,30 +79,30 @@ __device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV
         const long long base = c.row * g.Lxh;
         const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
         const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
-        const long long nf = base + (xp >> 1), nb = base + (xm >> 1);
+        const long long nf = LQ_IDX(base + (xp >> 1), g.Vh, B_HOP_NB), nb = LQ_IDX(base + (xm >> 1), g.Vh, B_HOP_NB);
         hop_dir<0, -1>(acc, in, Uout, s, nf, st, one);
         hop_dir<0, +1>(acc, in, Uin, nb, nb, st, one);
     }
     // y, z, t: x is unchanged, so the cb index moves by a fixed stride
     {
         const long long d = g.Lxh;
-        const long long nf = (c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d;
-        const long long nb = (c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d;
+        const long long nf = LQ_IDX((c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX((c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d, g.Vh, B_HOP_NB);
         hop_dir<1, -1>(acc, in, Uout, s, nf, st, one);
         hop_dir<1, +1>(acc, in, Uin, nb, nb, st, one);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1];
-        const long long nf = (c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d;
-        const long long nb = (c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d;
+        const long long nf = LQ_IDX((c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX((c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d, g.Vh, B_HOP_NB);
         hop_dir<2, -1>(acc, in, Uout, s, nf, st, one);
         hop_dir<2, +1>(acc, in, Uin, nb, nb, st, one);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1] * g.L[2];
         const bool last = (c.t + 1 == g.L[3]), first = (c.t == 0);
-        const long long nf = last ? s - (long long)(g.L[3] - 1) * d : s + d;
-        const long long nb = first ? s + (long long)(g.L[3] - 1) * d : s - d;
+        const long long nf = LQ_IDX(last ? s - (long long)(g.L[3] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX(first ? s + (long long)(g.L[3] - 1) * d : s - d, g.Vh, B_HOP_NB);
         const R tb = R(g.tbc);
         hop_dir<3, -1>(acc, in, Uout, s, nf, st, last ? tb : one);
         hop_dir<3, +1>(acc, in, Uin, nb, nb, st, first ? tb : one);
@@ -175,29 +175,29 @@ __device__ __forceinline__ void hop_body2(const Geom &g, const float4 *Uout, con
         const long long base = c.row * g.Lxh;
         const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
         const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
-        const long long nf = base + (xp >> 1), nb = base + (xm >> 1);
+        const long long nf = LQ_IDX(base + (xp >> 1), g.Vh, B_HOP_NB), nb = LQ_IDX(base + (xm >> 1), g.Vh, B_HOP_NB);
         hop_dir2<0, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
         hop_dir2<0, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
     }
     {
         const long long d = g.Lxh;
-        const long long nf = (c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d;
-        const long long nb = (c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d;
+        const long long nf = LQ_IDX((c.y + 1 == g.L[1]) ? s - (long long)(g.L[1] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX((c.y == 0) ? s + (long long)(g.L[1] - 1) * d : s - d, g.Vh, B_HOP_NB);
         hop_dir2<1, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
         hop_dir2<1, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1];
-        const long long nf = (c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d;
-        const long long nb = (c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d;
+        const long long nf = LQ_IDX((c.z + 1 == g.L[2]) ? s - (long long)(g.L[2] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX((c.z == 0) ? s + (long long)(g.L[2] - 1) * d : s - d, g.Vh, B_HOP_NB);
         hop_dir2<2, -1>(a0, a1, in0, in1, Uout, s, nf, st, 1.0f);
         hop_dir2<2, +1>(a0, a1, in0, in1, Uin, nb, nb, st, 1.0f);
     }
     {
         const long long d = (long long)g.Lxh * g.L[1] * g.L[2];
         const bool last = (c.t + 1 == g.L[3]), first = (c.t == 0);
-        const long long nf = last ? s - (long long)(g.L[3] - 1) * d : s + d;
-        const long long nb = first ? s + (long long)(g.L[3] - 1) * d : s - d;
+        const long long nf = LQ_IDX(last ? s - (long long)(g.L[3] - 1) * d : s + d, g.Vh, B_HOP_NB);
+        const long long nb = LQ_IDX(first ? s + (long long)(g.L[3] - 1) * d : s - d, g.Vh, B_HOP_NB);
         const float tb = (float)g.tbc;
         hop_dir2<3, -1>(a0, a1, in0, in1, Uout, s, nf, st, last ? tb : 1.0f);
         hop_dir2<3, +1>(a0, a1, in0, in1, Uin, nb, nb, st, first ? tb : 1.0f);
@@ -330,6 +330,167 @@ __global__ void LQ_GROUP_BOUNDS hop_group_kernel(const LatDesc *__restrict__ d,
     }
 }
 
+// The batched hop with a site block's links and clover blocks staged in shared
+// memory once for every right-hand side of its lattice.  A tile is (lattice,
+// block of S consecutive sites); the block has S x (128 / S) threads, thread
+// (x, y) owns site x of the block and walks right-hand sides y, y + 128/S, ...
+// Staging: for every site of the block, the four forward links U_mu(x), the
+// four backward links U_mu(x - mu) (read at the neighbour's index in the other
+// parity's link array) and the two packed clover blocks of the output parity:
+// 12 + 12 + 18 float4, laid out [entry][site] so that a warp's reads of one
+// entry are consecutive.  The links and clover thus cross DRAM once per site,
+// whatever the number of right-hand sides, and each right-hand side costs only
+// its spinor traffic.
+constexpr int kTileEntries = 42;   // float4 entries staged per site
+constexpr int kTileFwd = 0, kTileBwd = 12, kTileClov = 24;
+
+__device__ __forceinline__ void tile_link(const float4 *sm, int S, int e0, int x, cx<float> m[9])
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float4 t = sm[(e0 + k) * S + x];
+        m[2 * k] = {t.x, t.y};
+        m[2 * k + 1] = {t.z, t.w};
+    }
+    m[6] = cconj(cmul(m[1], m[5]) - cmul(m[2], m[4]));
+    m[7] = cconj(cmul(m[2], m[3]) - cmul(m[0], m[5]));
+    m[8] = cconj(cmul(m[0], m[4]) - cmul(m[1], m[3]));
+}
+
+// y = C x with both packed blocks of the site read from the staged entries
+__device__ __forceinline__ void tile_clover(const float4 *sm, int S, int x, const cx<float> in[12], cx<float> y[12])
+{
+#pragma unroll
+    for (int blk = 0; blk < 2; blk++) {
+        float a[36];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const float4 t = sm[(kTileClov + blk * 9 + k) * S + x];
+            a[4 * k] = t.x;
+            a[4 * k + 1] = t.y;
+            a[4 * k + 2] = t.z;
+            a[4 * k + 3] = t.w;
+        }
+        herm6_apply<float>(a, in + 6 * blk, y + 6 * blk);
+    }
+}
+
+template <int MU, int SIGN>
+__device__ __forceinline__ void tile_hop(cx<float> acc[12], const float4 *__restrict__ psi, long long st, int nb,
+                                         const float4 *sm, int S, int x, float bsign)
+{
+    cx<float> p[12];
+    load_spinor(psi, st, nb, p);
+    cx<float> m[9];
+    tile_link(sm, S, (SIGN < 0 ? kTileFwd : kTileBwd) + 3 * MU, x, m);
+    hop_apply<MU, SIGN>(acc, p, m, bsign);
+}
+
+template <int MODE, int S>
+__global__ void __launch_bounds__(LQ_HOP_THREADS, 5) hop_tile_kernel(const LatDesc *__restrict__ d,
+                                                                     const int4 *__restrict__ tiles, int ntiles,
+                                                                     const float4 *in, const float4 *in2, float4 *out)
+{
+    static_assert(MODE == HOP_K1 || MODE == HOP_K2, "K1 or K2");
+    constexpr int R = LQ_HOP_THREADS / S;   // right-hand-side lanes
+    constexpr int pout = MODE == HOP_K1 ? 1 : 0;
+    extern __shared__ float4 tile_sm[];
+    // after the staged entries: the eight neighbour indices of each site and its
+    // two time-boundary factors, [10][S] words (kept here rather than in
+    // registers across the loop over right-hand sides)
+    int *tile_nb = reinterpret_cast<int *>(tile_sm + kTileEntries * S);
+    float *tile_bc = reinterpret_cast<float *>(tile_nb + 8 * S);
+    const int x = threadIdx.x, y = threadIdx.y;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 w = __ldg(tiles + t);
+        const LatDesc *L = d + w.x;
+        const Geom g = L->g;
+        const long long st = g.stride;
+        const long long s = (long long)w.y * S + x;
+        const bool valid = s < g.Vh;
+        // neighbour checkerboard indices (forward, backward per direction) and
+        // the time-boundary factors; Vh < 2^31, so they fit an int
+        int nf[4], nb[4];
+        float tf = 1.0f, tb = 1.0f;
+        if (valid) {
+            const Coords c = cb_coords(g, s, pout);
+            const long long base = c.row * g.Lxh;
+            const int xp = (c.x + 1 == g.L[0]) ? 0 : c.x + 1;
+            const int xm = (c.x == 0) ? g.L[0] - 1 : c.x - 1;
+            nf[0] = (int)LQ_IDX(base + (xp >> 1), g.Vh, B_TILE_NB);
+            nb[0] = (int)LQ_IDX(base + (xm >> 1), g.Vh, B_TILE_NB);
+            long long dd = g.Lxh;
+            const int co[3] = {c.y, c.z, c.t};
+#pragma unroll
+            for (int mu = 1; mu < 4; mu++) {
+                const int ext = g.L[mu], q = co[mu - 1];
+                nf[mu] = (int)LQ_IDX((q + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd, g.Vh, B_TILE_NB);
+                nb[mu] = (int)LQ_IDX((q == 0) ? s + (long long)(ext - 1) * dd : s - dd, g.Vh, B_TILE_NB);
+                dd *= ext;
+            }
+            if (c.t + 1 == g.L[3]) tf = (float)g.tbc;
+            if (c.t == 0) tb = (float)g.tbc;
+        }
+        __syncthreads();   // the previous tile's reads of the staged entries are done
+        if (valid) {
+            const F4S *Uo = (const F4S *)L->U[pout];
+            const F4S *Ui = (const F4S *)L->U[1 - pout];
+            const F4S *Cl = (const F4S *)L->clov[pout];
+            for (int e = y; e < kTileEntries; e += R) {
+                const F4S *src;
+                if (e < kTileBwd) src = Uo + e * st + s;
+                else if (e < kTileClov) {
+                    const int mu = (e - kTileBwd) / 3;   // selected, not indexed: nb stays in registers
+                    const int n = mu == 0 ? nb[0] : mu == 1 ? nb[1] : mu == 2 ? nb[2] : nb[3];
+                    src = Ui + (long long)(e - kTileBwd) * st + n;
+                } else {
+                    src = Cl + (long long)(e - kTileClov) * st + s;
+                }
+                tile_sm[e * S + x] = ldg(src);
+            }
+            if (y == 0) {
+#pragma unroll
+                for (int mu = 0; mu < 4; mu++) {
+                    tile_nb[(2 * mu) * S + x] = nf[mu];
+                    tile_nb[(2 * mu + 1) * S + x] = nb[mu];
+                }
+                tile_bc[x] = tf;
+                tile_bc[S + x] = tb;
+            }
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int r = y; r < L->nrhs; r += R) {
+            const long long o = L->off + r * L->fs;
+            const float4 *pin = in + o;
+            cx<float> acc[12];
+#pragma unroll
+            for (int i = 0; i < 12; i++) acc[i] = {0.0f, 0.0f};
+            tile_hop<0, -1>(acc, pin, st, tile_nb[0 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<0, +1>(acc, pin, st, tile_nb[1 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<1, -1>(acc, pin, st, tile_nb[2 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<1, +1>(acc, pin, st, tile_nb[3 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<2, -1>(acc, pin, st, tile_nb[4 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<2, +1>(acc, pin, st, tile_nb[5 * S + x], tile_sm, S, x, 1.0f);
+            tile_hop<3, -1>(acc, pin, st, tile_nb[6 * S + x], tile_sm, S, x, tile_bc[x]);
+            tile_hop<3, +1>(acc, pin, st, tile_nb[7 * S + x], tile_sm, S, x, tile_bc[S + x]);
+            cx<float> v[12];
+            if (MODE == HOP_K1) {
+#pragma unroll
+                for (int i = 0; i < 12; i++) acc[i] = -0.5f * acc[i];
+                tile_clover(tile_sm, S, x, acc, v);
+            } else {
+                cx<float> xs[12];
+                load_spinor_rw(in2 + o, st, s, xs);
+                tile_clover(tile_sm, S, x, xs, v);
+#pragma unroll
+                for (int i = 0; i < 12; i++) v[i] = v[i] + 0.5f * acc[i];
+            }
+            store_spinor(out + o, st, s, v);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // df64 variant.  Each df64 operation is a chain of several FP32 instructions,
 // so the fully unrolled eight-direction body of hop_kernel would not fit the
@@ -397,15 +558,15 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
         flip = false;
         if (mu == 0) {
             const int xn = fwd ? (c.x + 1 == g.L[0] ? 0 : c.x + 1) : (c.x == 0 ? g.L[0] - 1 : c.x - 1);
-            return c.row * g.Lxh + (xn >> 1);
+            return (long long)LQ_IDX(c.row * g.Lxh + (xn >> 1), g.Vh, B_DF_NB);
         }
         const int coord = mu == 1 ? c.y : mu == 2 ? c.z : c.t;
         const int ext = g.L[mu];
         const long long dd = mu == 1 ? (long long)g.Lxh
                            : mu == 2 ? (long long)g.Lxh * g.L[1] : (long long)g.Lxh * g.L[1] * g.L[2];
         if (mu == 3) flip = g.tbc < 0 && (fwd ? coord + 1 == ext : coord == 0);
-        if (fwd) return (coord + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd;
-        return (coord == 0) ? s + (long long)(ext - 1) * dd : s - dd;
+        if (fwd) return (long long)LQ_IDX((coord + 1 == ext) ? s - (long long)(ext - 1) * dd : s + dd, g.Vh, B_DF_NB);
+        return (long long)LQ_IDX((coord == 0) ? s + (long long)(ext - 1) * dd : s - dd, g.Vh, B_DF_NB);
     };
 
 #pragma unroll 1
@@ -615,10 +776,21 @@ static const double c_hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 
 double hop_bytes(int mode, int prec, int nrhs, double sites) { return sites * hop_site_bytes(mode, prec, nrhs); }
 double hop_flops(int mode, double site_rhs) { return site_rhs * c_hop_flops[mode]; }
 
-int hop_group_resident(int rpt)
+// dynamic shared memory of the staged batched hop with S sites per tile
+static size_t tile_smem(int S) { return (size_t)kTileEntries * S * sizeof(float4) + 10 * S * sizeof(int); }
+
+int hop_group_resident(int rpt, int spt)
 {
     int a = 0, b = 0;
-    if (rpt == 2) {
+    if (rpt == 0) {
+        if (spt == 64) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_tile_kernel<HOP_K1, 64>, LQ_HOP_THREADS, tile_smem(64));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_tile_kernel<HOP_K2, 64>, LQ_HOP_THREADS, tile_smem(64));
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_tile_kernel<HOP_K1, 32>, LQ_HOP_THREADS, tile_smem(32));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_tile_kernel<HOP_K2, 32>, LQ_HOP_THREADS, tile_smem(32));
+        }
+    } else if (rpt == 2) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, hop_group_kernel<HOP_K1, 2>, LQ_HOP_THREADS, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_group_kernel<HOP_K2, 2>, LQ_HOP_THREADS, 0);
     } else {
@@ -636,6 +808,17 @@ void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, 
     const dim3 block(spt, LQ_HOP_THREADS / spt);
     const float4 *i1 = (const float4 *)in, *i2 = (const float4 *)in2;
     float4 *o = (float4 *)out;
+    if (rpt == 0) {   // staged links and clover, every right-hand side of the tile's lattice
+        const size_t sm = tile_smem(spt);
+        if (spt == 64) {
+            if (mode == HOP_K1) hop_tile_kernel<HOP_K1, 64><<<grid, block, sm, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+            else hop_tile_kernel<HOP_K2, 64><<<grid, block, sm, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+        } else {
+            if (mode == HOP_K1) hop_tile_kernel<HOP_K1, 32><<<grid, block, sm, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+            else hop_tile_kernel<HOP_K2, 32><<<grid, block, sm, e.st>>>(desc, tiles, ntiles, i1, i2, o);
+        }
+        return;
+    }
     if (mode == HOP_K1 && rpt == 2) hop_group_kernel<HOP_K1, 2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
     else if (mode == HOP_K1) hop_group_kernel<HOP_K1, 1><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);
     else if (rpt == 2) hop_group_kernel<HOP_K2, 2><<<grid, block, 0, e.st>>>(desc, tiles, ntiles, i1, i2, o);

@@ -97,14 +97,16 @@ __global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *
         for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * PER; w += TT) {
             const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
             typename Vec<PR>::T *f = p ? f1 : f0;
-            f[k * g.stride + s0 + j] = Vec<PR>::from(tile[tile_row<FULL>(par, j, p)], k);
+            f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)] =
+                Vec<PR>::from(tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
         }
     } else {            // the last, partial tile (rows is even on a full lattice)
         const int per = FULL ? rows / 2 : rows;
         for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * per; w += TT) {
             const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
             typename Vec<PR>::T *f = p ? f1 : f0;
-            f[k * g.stride + s0 + j] = Vec<PR>::from(tile[tile_row<FULL>(par, j, p)], k);
+            f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)] =
+                Vec<PR>::from(tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
         }
     }
 }
@@ -128,14 +130,16 @@ __global__ void __launch_bounds__(TT) export_tile_kernel(Geom g, const typename 
         for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * PER; w += TT) {
             const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
             const typename Vec<PR>::T *f = p ? f1 : f0;
-            Vec<PR>::to(f[k * g.stride + s0 + j], tile[tile_row<FULL>(par, j, p)], k);
+            Vec<PR>::to(f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)],
+                        tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
         }
     } else {
         const int per = FULL ? rows / 2 : rows;
         for (int w = threadIdx.x; w < (FULL ? 2 : 1) * NV * per; w += TT) {
             const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
             const typename Vec<PR>::T *f = p ? f1 : f0;
-            Vec<PR>::to(f[k * g.stride + s0 + j], tile[tile_row<FULL>(par, j, p)], k);
+            Vec<PR>::to(f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)],
+                        tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
         }
     }
     __syncthreads();
@@ -162,8 +166,8 @@ __global__ void __launch_bounds__(TT) import_links_kernel(Geom g, const double2 
     // 36 complex entries of FP64 and df64 per site, then 12 float4 of FP32
     auto put = [&](int j, int pk) {
         const int p = pk / 48, k = pk % 48;
-        const double2 *row = tile[tile_row<true>(par, j, p)];
-        const long long s = s0 + j;
+        const double2 *row = tile[LQ_IDX(tile_row<true>(par, j, p), rows, B_LAYOUT)];
+        const long long s = LQ_IDX(s0 + j, g.Vh, B_LAYOUT);
         if (k < 36) {   // k = mu * 9 + entry
             (p ? U64o : U64e)[k * g.stride + s] = row[k];
             (p ? Udfo : Udfe)[k * g.stride + s] = to_df2(row[k]);

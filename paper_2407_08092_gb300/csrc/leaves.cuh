@@ -34,7 +34,8 @@ static __constant__ unsigned char c_ldag[16] = {0, 0, 1, 1, 0, 1, 1, 0, 1, 1, 0,
 
 __device__ __forceinline__ long long lex_of(const Geom &g, const int c[4])
 {
-    return c[0] + (long long)g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
+    return LQ_IDX(c[0] + (long long)g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3])), g.V,
+                  B_LEX);
 }
 
 __device__ __forceinline__ void lex_coords(const Geom &g, long long lex, int c[4])

@@ -37,6 +37,54 @@ struct Geom {
 };
 
 // ---------------------------------------------------------------------------
+// Index checks of the checked build (compiled with -DLQ_BOUNDS).
+// LQ_IDX(i, n, code) is i when 0 <= i < n.  Otherwise the checked build
+// records the violation -- a count and the code of the first one, in device
+// flags of the translation unit -- and yields 0, so that the access stays
+// inside the buffer and nothing traps or faults; lq_bounds_check reads and
+// clears the flags of every translation unit.  The normal build compiles
+// LQ_IDX(i, n, code) to i.
+// ---------------------------------------------------------------------------
+enum BoundsSite : unsigned {
+    B_HOP_SITE = 1,   // output site of a hopping kernel
+    B_HOP_NB,         // neighbour index of the FP64 / FP32 / BF16 hopping kernels
+    B_DF_NB,          // neighbour index of the df64 hopping kernel
+    B_TILE_NB,        // neighbour index of the batched hopping kernels
+    B_SAP_LOCAL,      // block-local (shared-memory) index of the SAP kernel
+    B_SAP_GLOBAL,     // lattice index of the SAP kernel
+    B_LEX,            // lexicographic site of the clover and force kernels
+    B_LAYOUT          // natural / internal index of the layout kernels
+};
+#ifdef LQ_BOUNDS
+static __device__ unsigned int lq_bounds_count_tu;
+static __device__ unsigned int lq_bounds_first_tu;
+__device__ __forceinline__ long long lq_idx_checked(long long i, long long n, unsigned code)
+{
+    if (i >= 0 && i < n) return i;
+    if (atomicAdd(&lq_bounds_count_tu, 1u) == 0u) lq_bounds_first_tu = code;
+    return 0;
+}
+#define LQ_IDX(i, n, code) ::lq::lq_idx_checked((long long)(i), (long long)(n), (code))
+// host: every translation unit registers a reader of its flags
+void bounds_register(unsigned (*read_clear)(unsigned *first));
+#if !defined(__CUDA_ARCH__)
+static unsigned lq_bounds_read_clear_tu(unsigned *first)
+{
+    unsigned n = 0, f = 0, z = 0;
+    cudaMemcpyFromSymbol(&n, lq_bounds_count_tu, sizeof n);
+    cudaMemcpyFromSymbol(&f, lq_bounds_first_tu, sizeof f);
+    cudaMemcpyToSymbol(lq_bounds_count_tu, &z, sizeof z);
+    cudaMemcpyToSymbol(lq_bounds_first_tu, &z, sizeof z);
+    *first = f;
+    return n;
+}
+static const int lq_bounds_registered_tu = (bounds_register(&lq_bounds_read_clear_tu), 0);
+#endif
+#else
+#define LQ_IDX(i, n, code) (i)
+#endif
+
+// ---------------------------------------------------------------------------
 // double-float ("df64") arithmetic: an unevaluated sum hi + lo of two floats,
 // |lo| <= ulp(hi)/2, carrying about 48 significand bits.  GB300 executes FP32
 // at 64 times its FP64 rate, so FP64-accurate work runs faster in this form.

@@ -188,11 +188,15 @@ struct LatDesc {
 // threads per block of the hopping kernels
 constexpr int kHopBlock = 128;
 // resident blocks per SM of the batched hopping kernel with rpt (1 or 2)
-// right-hand sides per thread (for a persistent grid)
-int hop_group_resident(int rpt);
+// right-hand sides per thread, or of the staged form (rpt 0) with spt sites
+// per tile (for a persistent grid)
+int hop_group_resident(int rpt, int spt);
 // One work-table entry of the batched hopping launch: lattice, site block (of
 // blockDim.x sites) and first right-hand side (of rpt * blockDim.y, rpt
-// right-hand sides per thread sharing each link load).
+// right-hand sides per thread sharing each link load).  rpt 0 selects the staged
+// form: one entry per (lattice, site block of spt = 32 or 64 sites), whose links
+// and clover blocks are staged in shared memory and applied to every
+// right-hand side of the lattice (first right-hand side 0).
 // A persistent grid of `grid` blocks of (spt, kHopBlock / spt) threads
 // walks the table; mode HOP_K1 (odd output) or HOP_K2 (even output), FP32.
 void hop_group(const Exec &e, int mode, const LatDesc *desc, const int4 *tiles, int ntiles, int grid, int spt,

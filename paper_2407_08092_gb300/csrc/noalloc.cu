@@ -29,8 +29,9 @@ static_assert((long long)NA_MAX_BLOCKS * NA_CHUNK / 12 == LQ_NORM2_NOALLOC_MAX_S
 
 }  // namespace
 
-// The shared scratch: one partial sum per block.  Every GPU that loads the
-// library holds these 32 KiB until the process exits.  In host code this name
+// The shared scratch: one partial sum per block.  Every GPU on which the
+// library's module is loaded (under lazy module loading: by the first call on
+// that device) holds these 32 KiB until the process exits.  In host code this name
 // is only a host-side stand-in, so the host passes the device address obtained
 // from cudaGetSymbolAddress instead.
 static __device__ __align__(256) double lq_noalloc_scratch[NA_MAX_BLOCKS];
@@ -102,6 +103,10 @@ extern "C" lq_status lq_norm2_noalloc(const void *v, long long n_sites, double *
 {
     if (!out || n_sites < 0 || (n_sites > 0 && !v)) return LQ_ERR_ARG;
     if (n_sites > LQ_NORM2_NOALLOC_MAX_SITES) return LQ_ERR_ARG;
+    // A launch error left on this host thread by earlier work would otherwise be
+    // read (and cleared) by the check after our own launches: report it as
+    // LQ_ERR_CUDA before launching anything, and leave it in place for its owner.
+    if (cudaPeekAtLastError() != cudaSuccess) return LQ_ERR_CUDA;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
         cudaGetLastError();

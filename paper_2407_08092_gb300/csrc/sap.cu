@@ -63,7 +63,8 @@ __device__ __forceinline__ void sap_local(const SapArgs &a, int i, int p, int l[
 
 __device__ __forceinline__ long long sap_global_cb(const Geom &g, const int G[4])
 {
-    return (G[0] + (long long)g.L[0] * (G[1] + (long long)g.L[1] * (G[2] + (long long)g.L[2] * G[3]))) >> 1;
+    return LQ_IDX((G[0] + (long long)g.L[0] * (G[1] + (long long)g.L[1] * (G[2] + (long long)g.L[2] * G[3]))) >> 1,
+                  g.Vh, B_SAP_GLOBAL);
 }
 
 __device__ __forceinline__ void ld_sm(const float2 *f, int i, cx<float> v[12])
@@ -97,7 +98,8 @@ __device__ __forceinline__ void sap_hop_dir(const SapArgs &a, const float2 *src,
         if (!in) continue;
         int q[4] = {l[0], l[1], l[2], l[3]};
         q[MU] = (ln + ext) % ext;
-        const int nbi = (q[0] + a.b[0] * (q[1] + a.b[1] * (q[2] + a.b[2] * q[3]))) >> 1;
+        const int nbi = (int)LQ_IDX((q[0] + a.b[0] * (q[1] + a.b[1] * (q[2] + a.b[2] * q[3]))) >> 1, a.bvh,
+                                    B_SAP_LOCAL);
         cx<float> psi[12];
         ld_sm(src, nbi, psi);
         cx<float> m[9];
@@ -170,7 +172,8 @@ __device__ __forceinline__ void sap_face(const SapArgs &a, const int O[4], float
             hop_apply<MU, +1>(acc, psi, m, (MU == 3 && G[3] == 0) ? (float)a.g.tbc : 1.0f);
         }
         float2 *dst = p ? smO : smE;
-        const int ii = (l[0] + a.b[0] * (l[1] + a.b[1] * (l[2] + a.b[2] * l[3]))) >> 1;
+        const int ii = (int)LQ_IDX((l[0] + a.b[0] * (l[1] + a.b[1] * (l[2] + a.b[2] * l[3]))) >> 1, a.bvh,
+                                   B_SAP_LOCAL);
 #pragma unroll
         for (int c = 0; c < 12; c++) {
             float2 t = dst[c * SAP_THREADS + ii];

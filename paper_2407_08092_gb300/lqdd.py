@@ -11,9 +11,12 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblqdd.so")
+# LQ_LIBRARY may name another build of the same library (the index-checked
+# liblqdd_checked.so that the bounds tests load in a child process)
+LIB_PATH = os.environ.get("LQ_LIBRARY") or os.path.join(_HERE, "liblqdd.so")
 
-LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN, LQ_ERR_NAN, LQ_ERR_STATE = range(8)
+(LQ_OK, LQ_ERR_ARG, LQ_ERR_CUDA, LQ_ERR_OOM, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN, LQ_ERR_NAN, LQ_ERR_STATE,
+ LQ_ERR_BOUNDS) = range(9)
 LQ_F64, LQ_F32, LQ_DF64, LQ_BF16 = 0, 1, 2, 3
 LQ_OP_FULL, LQ_OP_SCHUR, LQ_OP_SCHUR_DAG, LQ_OP_EE, LQ_OP_OO_INV = range(5)
 LQ_SOLVER_GMRES, LQ_SOLVER_FGMRES = 0, 1
@@ -71,6 +74,9 @@ _lib.lq_profile_read.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longl
                                  ctypes.POINTER(ctypes.c_double)]
 _lib.lq_norm2_noalloc.argtypes = [_P, ctypes.c_longlong, _P, _P]
 _lib.lq_norm2_noalloc.restype = ctypes.c_int
+_lib.lq_bounds_check.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_ulonglong),
+                                 ctypes.POINTER(ctypes.c_int)]
+_lib.lq_bounds_check.restype = ctypes.c_int
 _lib.lq_kernel_class_name.argtypes = [ctypes.c_int]
 _lib.lq_kernel_class_name.restype = ctypes.c_char_p
 _lib.lq_last_error.argtypes = [_P]
@@ -162,6 +168,17 @@ def lq_norm2(ctx, v, n_sites: int) -> float:
 
 
 LQ_NORM2_NOALLOC_MAX_SITES = 2796202
+
+
+def lq_bounds_check():
+    """(status, checked, violations, first_code) of the checked build's index
+    checks since the last call (synchronises the device); status is LQ_OK or
+    LQ_ERR_BOUNDS and is returned, not raised."""
+    c, n, f = ctypes.c_int(), ctypes.c_ulonglong(), ctypes.c_int()
+    st = _lib.lq_bounds_check(ctypes.byref(c), ctypes.byref(n), ctypes.byref(f))
+    if st not in (LQ_OK, LQ_ERR_BOUNDS):
+        raise LqError(st, "lq_bounds_check")
+    return st, c.value, n.value, f.value
 
 
 def lq_norm2_noalloc(v, n_sites: int, out, stream: int | None = None) -> None:

@@ -26,6 +26,9 @@ def main():
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
     ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force", "sap"])
     ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--shape", default=None,
+                    help="batch mode: pin the batched hop's launch shape 'sites_per_tile,rhs_per_thread,grid_factor' "
+                         "instead of autotuning it")
     a = ap.parse_args()
     L = tuple(int(v) for v in a.lattice.split(","))
     V = int(np.prod(L))
@@ -54,6 +57,8 @@ def main():
             b[r, 0, r % 4, (r // 4) % 3] = 1.0
         x = torch.zeros_like(b)
         grp = lqdd.lq_group_create([ctx], torch.cuda.current_stream().cuda_stream)
+        if a.shape:
+            lqdd.lq_group_set_shape(grp, *(int(v) for v in a.shape.split(",")))
         for _ in range(a.apps):
             x.zero_()
             status, st = lqdd.lq_solve_group(grp, ctx, lqdd.make_batch_params(), [b], [x])

@@ -94,3 +94,19 @@ def test_product_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), fn
                 assert "liboracle" not in text, fn
+
+
+def test_unchecked_build_reports_no_index_checks(lib_path):
+    """lq_bounds_check in the normal build touches no device: checked = 0 and LQ_OK."""
+    from paper_2407_08092_gb300 import lqdd
+    status, checked, violations, first = lqdd.lq_bounds_check()
+    assert (status, checked, violations, first) == (lqdd.LQ_OK, 0, 0, 0)
+
+
+def test_checked_build_exports_the_same_symbols(lib_path):
+    """The index-checked build (-DLQ_BOUNDS) compiles and exports the same C ABI."""
+    from paper_2407_08092_gb300 import build
+    checked = build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", checked], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(lq_[a-z0-9_]+)$", out, flags=re.M))
+    assert exported == set(declared_functions())

@@ -131,14 +131,16 @@ def test_solve_group_uneven_lattices():
                     assert abs(r_true - stats[k].rel_resid_true) <= 1e-3 * r_true + 1e-15
                     k += 1
             spt, rpt, grid, blas, hop_ms, blas_ms = lqdd.lq_group_tuning(grp)
-            assert spt in (16, 32, 64, 128) and rpt in (1, 2) and grid >= 1 and blas >= 1
+            assert spt in (16, 32, 64, 128) and rpt in (0, 1, 2) and grid >= 1 and blas >= 1
+            assert rpt != 0 or spt in (32, 64)
             if autotune:
                 assert hop_ms > 0 and blas_ms > 0
             else:
                 assert (spt, rpt, hop_ms, blas_ms) == (32, 1, 0.0, 0.0)
         # every pinned launch shape (two right-hand sides per thread with odd counts
-        # included) gives converged solutions
-        for spt, rpt, fac in [(32, 2, 1), (128, 2, 0), (16, 1, 2), (64, 2, 2)]:
+        # included, and the staged form whose tiles cover every right-hand side)
+        # gives converged solutions
+        for spt, rpt, fac in [(32, 2, 1), (128, 2, 0), (16, 1, 2), (64, 2, 2), (32, 0, 1), (64, 0, 2), (32, 0, 0)]:
             lqdd.lq_group_set_shape(grp, spt, rpt, fac)
             xs2 = [p.torch.zeros_like(d) for p, d in zip(pairs, db)]
             status, stats = lqdd.lq_solve_group(grp, pairs[0].ctx, lqdd.make_batch_params(tol=1e-10), db, xs2)
@@ -171,6 +173,9 @@ def test_solve_group_status_codes():
         try:
             with pytest.raises(lqdd.LqError):
                 lqdd.lq_group_tuning(grp)                   # no solve yet
+            with pytest.raises(lqdd.LqError) as ei:          # the staged form takes 32 or 64 sites per tile
+                lqdd.lq_group_set_shape(grp, 16, 0, 1)
+            assert ei.value.status == lqdd.LQ_ERR_ARG
             da = a.dev(sources(a.lat, 2, 11))
             dbb = b.dev(sources(b.lat, 1, 12))
             xa, xb = a.torch.zeros_like(da), b.torch.zeros_like(dbb)
