@@ -924,6 +924,11 @@ def run_ours(args):
             "sap34_ms": sap["sap_3_4_ms"], "rich5_ms": sap["richardson_5_ms"], "fgmres_sap_ms": sap["fgmres_sap_ms"],
             "frac": (sap.get("roofline") or {}).get("frac")},
         "bf16": None if bf16 is None else pick(bf16["bf16"], "ds_us", "ds_frac", "rel_err_vs_fp64"),
+        # df64 classes against the SMs' instruction-issue ceiling (ncu-counted
+        # instructions per launch over the live launch time); the 15-instruction
+        # flop model beside it
+        "df64_issue": {k: {"frac": v["frac"], "model_frac": v["df64_model_frac"]}
+                       for k, v in ops.items() if v.get("bound") == "issue"},
         "detail": args.detail,
     }
     print(json.dumps(line), flush=True)

@@ -59,18 +59,20 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert r.stdout.strip() == ""
 
 
-def test_traffic_table_rows_and_staleness(tmp_path, monkeypatch):
-    """profiles/traffic.txt: every row names a kernel class of the library, a
-    per-site unit and an existing source file; bench.traffic_per_launch scales
-    the per-site bytes to a launch while the source is unchanged and reports
-    None once the file's hash differs from the one captured."""
+@pytest.mark.parametrize("table", ["traffic.txt", "issue.txt"])
+def test_ncu_table_rows_and_staleness(tmp_path, monkeypatch, table):
+    """profiles/traffic.txt (DRAM bytes) and profiles/issue.txt (warp
+    instructions): every row names a kernel class of the library, a per-site
+    unit and an existing source file; bench.table_per_launch scales the
+    per-site value to a launch while the source is unchanged and reports None
+    once the file's hash differs from the one captured."""
     sys.path.insert(0, ROOT)
     import bench
     from paper_2407_08092_gb300 import build
     build.build()   # the class names come from the library (a no-op when it is up to date)
     from paper_2407_08092_gb300 import lqdd
     classes = {lqdd.lq_kernel_class_name(c) for c in range(lqdd.LQ_K_COUNT)}
-    rows = [ln.split() for ln in open(os.path.join(ROOT, "profiles", "traffic.txt")) if ln.strip() and ln[0] != "#"]
+    rows = [ln.split() for ln in open(os.path.join(ROOT, "profiles", table)) if ln.strip() and ln[0] != "#"]
     assert rows
     for name, per_unit, unit, src, digest in rows:
         assert name in classes, name
@@ -78,14 +80,14 @@ def test_traffic_table_rows_and_staleness(tmp_path, monkeypatch):
         assert os.path.exists(os.path.join(ROOT, "paper_2407_08092_gb300", "csrc", src))
     # the live table: bytes per launch proportional to the sites (None when stale)
     name, per_unit, unit, src, _ = rows[0]
-    got = bench.traffic_per_launch(name, 2 * 1024)
+    got = bench.table_per_launch(table, name, 2 * 1024)
     if got is not None:
         assert got == pytest.approx(float(per_unit) * (2048 if unit == "V" else 1024))
     # a copy of the tree whose source file no longer matches: None
     fake = tmp_path / "root"
     (fake / "profiles").mkdir(parents=True)
     (fake / "paper_2407_08092_gb300" / "csrc").mkdir(parents=True)
-    (fake / "profiles" / "traffic.txt").write_text(f"{name} {per_unit} {unit} {src} 0123456789abcdef\n")
+    (fake / "profiles" / table).write_text(f"{name} {per_unit} {unit} {src} 0123456789abcdef\n")
     (fake / "paper_2407_08092_gb300" / "csrc" / src).write_text("// changed\n")
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    assert bench.traffic_per_launch(name, 2048) is None
+    assert bench.table_per_launch(table, name, 2048) is None
