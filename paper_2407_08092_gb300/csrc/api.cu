@@ -1393,7 +1393,8 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
         // follow on first use)
         import_links(e, U, c->U64, c->U32, c->Udf);
         const void *udf[2] = {c->Udf[0], c->Udf[1]};
-        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C32, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V));
+        clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C32, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V),
+                     ws(c, "clover:R", (size_t)6 * 9 * 8 * g.V));
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
         clover_invert(e, c->Cdf[1], c->Cidf, c->Ci32, c->dflag);
         ck_launch(c, "set_gauge kernels");

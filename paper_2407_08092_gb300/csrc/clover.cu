@@ -15,9 +15,10 @@
 // The library builds and inverts in df64 (FP64-accurate, on the FP32 units,
 // which GB300 runs at 64 times its FP64 rate); the assembly and inverse kernels
 // also write the FP32 copies, rounded from df64.  The FP64 copies are rounded
-// from df64 by clover_to_f64 when an FP64 operator first needs them.  The build is split in two launches: one thread per
-// (site, plane) computes the four leaves and F of that plane into a scratch
-// array, then one thread per site assembles the two 6x6 blocks.
+// from df64 by clover_to_f64 when an FP64 operator first needs them.  The
+// field strengths F of the six planes come from three passes over plaquettes
+// (one thread per (site, plane) each, into scratch arrays), then one thread
+// per site assembles the two 6x6 blocks.
 #include "leaves.cuh"
 #include "lq_kernels.h"
 
@@ -43,60 +44,167 @@ __device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.
 __device__ __forceinline__ bool positive(double d) { return d > 0.0; }
 __device__ __forceinline__ bool positive(df64 d) { return df_positive(d); }
 
-// Field strength of one plane at one site per thread: F = (Q - Q^+)/8 is
-// anti-Hermitian, so 9 reals describe it: Im F_aa (a = 0,1,2), then F_01, F_02,
-// F_12 (re, im).  Stored as df64 pairs in F[plane][9][V].  The leaf factors
-// come from the tables of leaves.cuh.
-__global__ void __launch_bounds__(128) clover_field_kernel(Geom g, const df2 *__restrict__ Ue,
-                                                           const df2 *__restrict__ Uo, float2 *Fb)
+// ---------------------------------------------------------------------------
+// The field strengths in three passes over plaquettes.  Each of the four
+// leaves at x is the plaquette of a neighbouring corner rotated to start at x,
+// and the anti-Hermitian part AH(M) = M - M^+ commutes with that unitary
+// rotation, so with P(y) = U_mu(y) U_nu(y+mu) U_mu(y+nu)^+ U_nu(y)^+:
+//   pass 1  H(y) = AH(P(y))
+//   pass 2  R(y) = H(y) + U_mu(y-mu)^+ H(y-mu) U_mu(y-mu)       (leaves 1, 2)
+//   pass 3  F(x) = [R(x) + U_nu(x-nu)^+ R(x-nu) U_nu(x-nu)] / 8 (leaves 1..4)
+// which is F = (Q - Q^+)/8 with Q the sum of the four leaves.  Per (site,
+// plane) this takes two full 3x3 products and one anti-Hermitian-only product
+// in pass 1 and one product plus one anti-Hermitian-only product in each of
+// passes 2 and 3, against twelve full products for the four leaves formed one
+// by one.  H, R and F are anti-Hermitian and stored as 9 reals (df64 pairs in
+// [plane][9][V] float2: Im A_aa, then A_01, A_02, A_12).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void site_coords(const Geom &g, long long lex, int c[4])
+{
+    long long r = lex;
+    c[0] = (int)(r % g.L[0]);
+    r /= g.L[0];
+    c[1] = (int)(r % g.L[1]);
+    r /= g.L[1];
+    c[2] = (int)(r % g.L[2]);
+    c[3] = (int)(r / g.L[2]);
+}
+
+// coordinates c shifted by s (-1, 0, +1) along mu
+__device__ __forceinline__ void shifted(const Geom &g, const int c[4], int mu, int s, int out[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++) out[k] = c[k];
+    const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+    int v = (mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3]) + s;
+    v = v < 0 ? v + L : (v >= L ? v - L : v);
+    if (mu == 0) out[0] = v;
+    else if (mu == 1) out[1] = v;
+    else if (mu == 2) out[2] = v;
+    else out[3] = v;
+}
+
+// A B^+ (full product), each entry a lazily normalised compensated sum
+__device__ __forceinline__ M3<df64> mat_mul_nd(const M3<df64> &A, const M3<df64> &B)
+{
+    M3<df64> P;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            // sum_k A_ak conj(B_bk) = sum_k conj(B_bk) A_ak
+            cx<df64> acc = dl_cmul(cconj(B.a[b * 3]), A.a[a * 3]);
+            dl_cfmac(acc, B.a[b * 3 + 1], A.a[a * 3 + 1]);
+            dl_cfmac(acc, B.a[b * 3 + 2], A.a[a * 3 + 2]);
+            P.a[a * 3 + b] = dl_cnorm(acc);
+        }
+    return P;
+}
+
+// the 9 reals of AH(A B^+): Im 2 (A B^+)_aa, then (A B^+)_ab - conj((A B^+)_ba) for a < b
+__device__ __forceinline__ void ah_of_mul_nd(const M3<df64> &A, const M3<df64> &B, df64 v[9])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {   // Im sum_k A_ak conj(B_ak) = sum_k (A.im B.re - A.re B.im)
+        df64 s = dl_prod(A.a[a * 3].im, B.a[a * 3].re);
+        dl_fma(s, dl_neg(A.a[a * 3].re), B.a[a * 3].im);
+#pragma unroll
+        for (int k = 1; k < 3; k++) {
+            dl_fma(s, A.a[a * 3 + k].im, B.a[a * 3 + k].re);
+            dl_fma(s, dl_neg(A.a[a * 3 + k].re), B.a[a * 3 + k].im);
+        }
+        v[a] = dl_scale2(dl_norm(s), 2.0f);
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const int a = pa[q], b = pb[q];
+        // X = sum_k A_ak conj(B_bk), Y = sum_k A_bk conj(B_ak); AH_ab = X - conj(Y)
+        cx<df64> x = dl_cmul(cconj(B.a[b * 3]), A.a[a * 3]), y = dl_cmul(cconj(B.a[a * 3]), A.a[b * 3]);
+#pragma unroll
+        for (int k = 1; k < 3; k++) {
+            dl_cfmac(x, B.a[b * 3 + k], A.a[a * 3 + k]);
+            dl_cfmac(y, B.a[a * 3 + k], A.a[b * 3 + k]);
+        }
+        dl_add(x.re, dl_neg(y.re));
+        dl_add(x.im, y.im);
+        v[3 + 2 * q] = dl_norm(x.re);
+        v[4 + 2 * q] = dl_norm(x.im);
+    }
+}
+
+// the 9 reals of W^+ H W for an anti-Hermitian H (itself anti-Hermitian)
+__device__ __forceinline__ void ah_conj(const M3<df64> &H, const M3<df64> &W, df64 v[9])
+{
+    const M3<df64> Y = mat_mul<df64>(H, W);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {   // Im sum_k conj(W_ka) Y_ka = sum_k (W.re Y.im - W.im Y.re)
+        df64 s = dl_prod(W.a[a].re, Y.a[a].im);
+        dl_fma(s, dl_neg(W.a[a].im), Y.a[a].re);
+#pragma unroll
+        for (int k = 1; k < 3; k++) {
+            dl_fma(s, W.a[k * 3 + a].re, Y.a[k * 3 + a].im);
+            dl_fma(s, dl_neg(W.a[k * 3 + a].im), Y.a[k * 3 + a].re);
+        }
+        v[a] = dl_norm(s);
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const int a = pa[q], b = pb[q];
+        cx<df64> z = dl_cmul(cconj(W.a[a]), Y.a[b]);   // sum_k conj(W_ka) Y_kb
+#pragma unroll
+        for (int k = 1; k < 3; k++) dl_cfmac(z, W.a[k * 3 + a], Y.a[k * 3 + b]);
+        v[3 + 2 * q] = dl_norm(z.re);
+        v[4 + 2 * q] = dl_norm(z.im);
+    }
+}
+
+// pass 1: H(y) = AH(P(y)), one thread per (site, plane)
+__global__ void __launch_bounds__(128) clover_plaq_kernel(Geom g, const df2 *__restrict__ Ue,
+                                                          const df2 *__restrict__ Uo, float2 *H)
 {
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 6 * g.V) return;
     const int p = (int)(id / g.V);
     const long long lex = id - p * g.V;
-    int c[4];
-    {
-        long long r = lex;
-        c[0] = (int)(r % g.L[0]); r /= g.L[0];
-        c[1] = (int)(r % g.L[1]); r /= g.L[1];
-        c[2] = (int)(r % g.L[2]); c[3] = (int)(r / g.L[2]);
-    }
+    int c[4], cm[4], cn[4];
+    site_coords(g, lex, c);
     const int mu = c_pmu[p], nu = c_pnu[p];
-    M3<df64> Q;
+    shifted(g, c, mu, +1, cm);
+    shifted(g, c, nu, +1, cn);
+    const M3<df64> T1 = mat_mul<df64>(link_at<df64>(g, Ue, Uo, c, mu), link_at<df64>(g, Ue, Uo, cm, nu));
+    const M3<df64> T2 = mat_mul_nd(T1, link_at<df64>(g, Ue, Uo, cn, mu));
+    df64 v[9];
+    ah_of_mul_nd(T2, link_at<df64>(g, Ue, Uo, c, nu), v);
+    store_antiherm(H, g.V, lex, p, v);
+}
+
+// passes 2 and 3: Out(x) = scale [In(x) + W^+ In(x - e) W], W = U_e(x - e) with
+// e = mu (pass 2) or nu (pass 3) of the thread's plane
+template <bool NU>
+__global__ void __launch_bounds__(128) clover_rot_kernel(Geom g, const df2 *__restrict__ Ue,
+                                                         const df2 *__restrict__ Uo, const float2 *__restrict__ In,
+                                                         float2 *Out, float scale)
+{
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= 6 * g.V) return;
+    const int p = (int)(id / g.V);
+    const long long lex = id - p * g.V;
+    int c[4], cs[4];
+    site_coords(g, lex, c);
+    const int e = NU ? c_pnu[p] : c_pmu[p];
+    shifted(g, c, e, -1, cs);
+    df64 v[9];
+    ah_conj(load_antiherm(In, g.V, lex_of(g, cs), p), link_at<df64>(g, Ue, Uo, cs, e), v);
+    df64 w[9];
 #pragma unroll
-    for (int k = 0; k < 9; k++) Q.a[k] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
-#pragma unroll 1
-    for (int leaf = 0; leaf < 4; leaf++) {
-        M3<df64> T;
-#pragma unroll 1
-        for (int i = 0; i < 4; i++) {
-            const int f = 4 * leaf + i;
-            int cc[4] = {c[0], c[1], c[2], c[3]};
-            cc[mu] = (cc[mu] + c_ldmu[f] + g.L[mu]) % g.L[mu];
-            cc[nu] = (cc[nu] + c_ldnu[f] + g.L[nu]) % g.L[nu];
-            M3<df64> Lk = link_at<df64>(g, Ue, Uo, cc, c_lnu[f] ? nu : mu);
-            if (c_ldag[f]) {
-                M3<df64> d;
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-#pragma unroll
-                    for (int b = 0; b < 3; b++) d.a[a * 3 + b] = cconj(Lk.a[b * 3 + a]);
-                Lk = d;
-            }
-            T = i == 0 ? Lk : mat_mul(T, Lk);
-        }
-#pragma unroll
-        for (int k = 0; k < 9; k++) dl_cadd(Q.a[k], T.a[k]);   // renormalised after the four leaves
+    for (int k = 0; k < 9; k++) {
+        const float2 t = __ldg(In + ((long long)p * 9 + k) * g.V + lex);
+        df64 sum = df64(t.x, t.y) + v[k];
+        w[k] = dl_scale2(sum, scale);   // scale 1 or 1/8: exact
     }
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.a[k] = dl_cnorm(Q.a[k]);
-    // F = (Q - Q^+)/8: Im F_aa, then F_01, F_02, F_12
-    const df64 eighth(0.125f, 0.0f);
-    auto fa = [&](int a, int b) { return eighth * (Q.a[a * 3 + b] - cconj(Q.a[b * 3 + a])); };
-    const cx<df64> f01 = fa(0, 1), f02 = fa(0, 2), f12 = fa(1, 2);
-    const df64 v[9] = {fa(0, 0).im, fa(1, 1).im, fa(2, 2).im, f01.re, f01.im, f02.re, f02.im, f12.re, f12.im};
-#pragma unroll
-    for (int k = 0; k < 9; k++) Fb[((long long)p * 9 + k) * g.V + lex] = make_float2(v[k].hi, v[k].lo);
+    store_antiherm(Out, g.V, lex, p, w);
 }
 
 // entry (a, b) of the anti-Hermitian F of plane p at site lex
@@ -304,16 +412,32 @@ __global__ void clover_export_kernel(Geom g, const double2 *__restrict__ Ce, con
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C32[2],
-                  void *Fscratch)
+                  void *Fscratch, void *Rscratch)
 {
     {
-        // unique bytes per site: its four df64 links (4 x 144) and the six F
-        // (6 x 72); per (site, plane): 12 complex 3x3 products of 198 flops,
-        // the leaf sum and (Q - Q^+)/8
-        Launch L_(e, K_CLOVER_FIELD, (double)e.g.V * (4 * 144 + 6 * 72), (double)e.g.V * 6 * (12 * 198 + 54 + 36));
-        clover_field_kernel<<<blocks_for(6 * e.g.V, 128), 128, 0, e.st>>>(e.g, (const df2 *)Udf[0],
-                                                                                (const df2 *)Udf[1],
-                                                                                (float2 *)Fscratch);
+        // the field strengths in three passes (H into Fscratch, R into Rscratch,
+        // F into Fscratch).  Unique bytes per site and pass: its four df64 links
+        // (4 x 144), the six anti-Hermitian matrices read (6 x 72, passes 2, 3)
+        // and written (6 x 72).  Flops per (site, plane): pass 1 two 3x3
+        // products (2 x 198) and AH(A B^+) (3 x 12 + 3 x 48); passes 2 and 3
+        // one product (198), the anti-Hermitian part of W^+ Y (3 x 12 + 3 x 24)
+        // and the sum (9)
+        const unsigned nb = blocks_for(6 * e.g.V, 128);
+        const df2 *U0 = (const df2 *)Udf[0], *U1 = (const df2 *)Udf[1];
+        {
+            Launch L_(e, K_CLOVER_FIELD, (double)e.g.V * (4 * 144 + 6 * 72), (double)e.g.V * 6 * (2 * 198 + 180));
+            clover_plaq_kernel<<<nb, 128, 0, e.st>>>(e.g, U0, U1, (float2 *)Fscratch);
+        }
+        {
+            Launch L_(e, K_CLOVER_FIELD, (double)e.g.V * (4 * 144 + 2 * 6 * 72), (double)e.g.V * 6 * (198 + 117));
+            clover_rot_kernel<false><<<nb, 128, 0, e.st>>>(e.g, U0, U1, (const float2 *)Fscratch, (float2 *)Rscratch,
+                                                           1.0f);
+        }
+        {
+            Launch L_(e, K_CLOVER_FIELD, (double)e.g.V * (4 * 144 + 2 * 6 * 72), (double)e.g.V * 6 * (198 + 117));
+            clover_rot_kernel<true><<<nb, 128, 0, e.st>>>(e.g, U0, U1, (const float2 *)Rscratch, (float2 *)Fscratch,
+                                                          0.125f);
+        }
     }
     // reads the six F, writes the blocks in df64 and FP32
     Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * (8 + 4)));

@@ -106,10 +106,10 @@ void gamma5(const Exec &e, int prec, const void *in, void *out);
 
 // ---- clover (clover.cu) ----------------------------------------------------
 // C(x) of every site from the internal df64 links: packed blocks per parity in
-// df64 and, rounded, FP32; Fscratch: device scratch of 6 * 9 * V * 8 bytes
-// (the six field strengths)
+// df64 and, rounded, FP32; Fscratch, Rscratch: device scratch of 6 * 9 * V * 8
+// bytes each (the six field strengths and the half-clover sums of the passes)
 void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void *Cdf[2], void *C32[2],
-                  void *Fscratch);
+                  void *Fscratch, void *Rscratch);
 // inverse of the blocks of one parity by LDL^+ in df64, written in df64 and
 // FP32; *flag += failures
 void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci32, int *flag);

@@ -6,8 +6,8 @@ GB) and then either applies D_S (K1 + K2) `--apps` times in one precision
 through the C ABI (printing per-class device times), runs `--apps`
 mixed-precision solves (FGMRES(10) in df64 preconditioned by GMRES(8) in
 FP32), a batched solve of `--nrhs` point sources through a one-member group
-(printing the autotuner's choice), SAP(3, 4) smoother calls, or the
-fermion-force kernel, e.g.
+(printing the autotuner's choice), SAP(3, 4) smoother calls, the
+fermion-force kernel, or lq_set_gauge (the clover build), e.g.
 ``python -m paper_2407_08092_gb300.profile_case --lattice 24,24,24,48 --prec 1 --apps 3``.
 """
 import argparse
@@ -24,7 +24,7 @@ def main():
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32, 2 df64")
     ap.add_argument("--apps", type=int, default=3)
     ap.add_argument("--op", type=int, default=lqdd.LQ_OP_SCHUR)
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force", "sap"])
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "batch", "force", "sap", "gauge"])
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--shape", default=None,
                     help="batch mode: pin the batched hop's launch shape 'sites_per_tile,rhs_per_thread,grid_factor' "
@@ -89,6 +89,23 @@ def main():
                       f"{by / (ms * 1e6):8.1f} GB/s")
         lqdd.lq_profile(ctx, 0)
         out = float(e.abs().sum())
+    elif a.mode == "gauge":   # lq_set_gauge: layout, clover field, assembly and inverse
+        U = torch.from_numpy(synth.gauge_links(L, 0.25, 1003)).cuda()
+        lqdd.lq_profile(ctx, 1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(a.apps):
+            lqdd.lq_set_gauge(ctx, U)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("set_gauge", round(ev[0].elapsed_time(ev[1]) / a.apps, 3), "ms per call")
+        for c in range(lqdd.LQ_K_COUNT):
+            nl, ms, by, fl = lqdd.lq_profile_read(ctx, c)
+            if nl:
+                print(f"{lqdd.lq_kernel_class_name(c):14s} {nl:5d} launches {1e3 * ms / nl:9.2f} us/launch "
+                      f"{by / (ms * 1e6):8.1f} GB/s {fl / (ms * 1e9):8.3f} TFLOP/s")
+        lqdd.lq_profile(ctx, 0)
+        out = 0.0
     elif a.mode == "force":
         X = torch.from_numpy(synth.gaussian_spinor(V, 71)).cuda()
         Y = torch.from_numpy(synth.gaussian_spinor(V, 72)).cuda()

@@ -245,6 +245,50 @@ def test_clover_from_paired_leaves():
     assert np.abs(lat.C - (4 + lat.m0) * np.eye(12)).max() > 1e-2
 
 
+def test_clover_from_rotated_plaquettes():
+    """C(x) rebuilt from plaquettes only, in three passes: each leaf at x is the
+    plaquette of a neighbouring corner rotated to start at x, and the
+    anti-Hermitian part AH(M) = M - M^+ commutes with that unitary rotation, so
+    with P(y) = U_mu(y) U_nu(y+mu) U_mu(y+nu)^+ U_nu(y)^+:
+      R(y) = AH(P(y)) + U_mu(y-mu)^+ AH(P(y-mu)) U_mu(y-mu)      (leaves 1, 2)
+      F(x) = [R(x) + U_nu(x-nu)^+ R(x-nu) U_nu(x-nu)] / 8        (leaves 1..4)
+    and C = (4 + m0) + c_sw (i/2) sum_{mu<nu} sigma_mu_nu (x) F_mu_nu equals the
+    oracle's clover term, which sums the four leaves directly."""
+    L = (4, 2, 4, 6)
+    lat = rand_lattice(L, seed=47, eps=0.7, csw=1.3)
+    U, c = lat.U, coords(L)
+    dag = lambda m: np.conj(np.swapaxes(m, -1, -2))
+    mm = lambda *ms: ms[0] if len(ms) == 1 else np.einsum("nab,nbc->nac", ms[0], mm(*ms[1:]))
+    AH = lambda m: m - dag(m)
+
+    def idx(d):      # the site x + d of every site x
+        cc = (c + np.asarray(d)) % np.asarray(L)
+        return cc[:, 0] + L[0] * (cc[:, 1] + L[1] * (cc[:, 2] + L[2] * cc[:, 3]))
+
+    def e(mu, k=1):
+        v = np.zeros(4, dtype=int)
+        v[mu] = k
+        return v
+
+    g = [oracle.gamma(mu) for mu in range(4)]
+    C = np.zeros((lat.V, 12, 12), dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            m, n = e(mu), e(nu)
+            Umu, Unu = U[:, mu], U[:, nu]
+            P = mm(Umu, Unu[idx(m)], dag(Umu[idx(n)]), dag(Unu))
+            Hp = AH(P)
+            W = Umu[idx(-m)]
+            R = Hp + mm(dag(W), Hp[idx(-m)], W)
+            W = Unu[idx(-n)]
+            F = (R + mm(dag(W), R[idx(-n)], W)) / 8
+            sigma = 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+            C += 0.5j * lat.csw * np.einsum("st,nab->nsatb", sigma, F).reshape(lat.V, 12, 12)
+    C += (4 + lat.m0) * np.eye(12)
+    assert np.abs(C - lat.C).max() < 1e-13
+    assert np.abs(lat.C - (4 + lat.m0) * np.eye(12)).max() > 1e-2
+
+
 def test_clover_structure_and_inverse():
     """C is Hermitian, commutes with g5 (two 6x6 blocks), and C C^{-1} = 1."""
     lat = rand_lattice((4, 4, 4, 2), seed=41, eps=0.9, csw=1.9)
