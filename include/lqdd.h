@@ -120,7 +120,9 @@ typedef struct {
     int cycles;              /* restart cycles of the (outer) solver */
     int iters;               /* Arnoldi steps of the (outer) solver */
     long long inner_iters;   /* D_S applications inside smoother / preconditioner calls */
-    double rel_resid;        /* ||b_hat_e - D_S x_e|| / ||b|| at exit, recomputed in FP64 or df64 */
+    double rel_resid;        /* ||b_hat_e - D_S x_e|| / ||b|| at exit (FP64 or df64): recomputed when
+                                the solver ran out of cycles; when it stopped on its least-squares
+                                estimate, the full residual below, which equals it after Eq. 2 */
     double rel_resid_true;   /* ||b - D x|| / ||b|| on the full lattice, FP64 */
     double time_ms;          /* host wall time of the call */
     double bytes;            /* algorithmic bytes of every kernel the call launched */
@@ -185,7 +187,11 @@ lq_status lq_norm2(lq_ctx *ctx, const void *v, long long n_sites, double *out);
 lq_status lq_smooth(lq_ctx *ctx, const lq_solver_params *params, const void *r, void *e);
 
 /* Solve D x = b by odd-even reduction (Eq. 2): prepare, solve the Schur system
- * with the method in params, reconstruct.  x holds the initial guess on entry
+ * with the method in params, reconstruct.  The Krylov solver stops once its
+ * least-squares estimate of the residual reaches tol ||b||; convergence is then
+ * decided on the full system's residual ||b - D x|| recomputed after the
+ * reconstruction, and the solve resumes (within max_restarts cycles) if that
+ * residual still exceeds the tolerance.  x holds the initial guess on entry
  * (its even half starts the iteration; pass zeros for none) and the solution on
  * exit.  b, x: full spinors.  stats may be NULL.  Synchronises.
  * LQ_ERR_NOT_CONVERGED still writes the last iterate and fills stats. */

@@ -432,9 +432,7 @@ double arnoldi_scaled(lq_ctx *c, void *V, int k, void *w, Hess &H, double *s)
     Exec e = c->ex();
     const int n = k + 1;
     multi_dot(e, P32, V, n, w, c->red, 0);
-    reduce_finish(e, c->red, 0, n, c->d_s2);
-    multi_axpy(e, P32, V, n, c->red.out, -1, w, &c->red, n);
-    reduce_finish(e, c->red, n, 1);
+    multi_axpy_finish(e, V, n, c->red, c->d_s2, -1, w, n);   // finishes the dots and the new norm itself
     ck_launch(c, "arnoldi");
     const double *hv = fetch(c, 0, n + 1);
     for (int j = 0; j < n; j++) H.h(j, k) = cd(hv[2 * j], hv[2 * j + 1]) * (s[k] / s[j]);
@@ -448,8 +446,13 @@ double arnoldi_scaled(lq_ctx *c, void *V, int k, void *w, Hess &H, double *s)
 // Restarted GMRES(m) on D_S in precision `prec`: b, x internal even fields.
 // x_zero: x is known to be zero on entry (skips the first residual product).
 // tol > 0 stops at ||b - D_S x|| <= tol ||b||; tol == 0 runs max_cycles full cycles.
+// confirm: a cycle whose least-squares estimate reaches the tolerance is
+// confirmed by the recomputed residual before returning (the next cycle's
+// first step); without it the call returns on the estimate, for callers that
+// check the result themselves (the odd-even solve recomputes the full
+// system's residual) or only precondition with it.
 KResult gmres(lq_ctx *c, int prec, const void *b, void *x, int m, int max_cycles, double tol, bool x_zero,
-              const char *wsname, double bnorm_hint = -1.0)
+              const char *wsname, double bnorm_hint = -1.0, bool confirm = true)
 {
     Exec e = c->ex();
     KResult R;
@@ -516,8 +519,11 @@ KResult gmres(lq_ctx *c, int prec, const void *b, void *x, int m, int max_cycles
         ck_launch(c, "gmres update");
         x_zero = false;
         if (tol > 0 && R.relres <= tol) {
-            // confirm with the recomputed residual before declaring convergence
-            continue;
+            if (!confirm) {   // the estimate reached the tolerance: the caller checks
+                R.converged = true;
+                return R;
+            }
+            continue;   // confirm with the recomputed residual before declaring convergence
         }
     }
     if (tol > 0) {
@@ -647,7 +653,7 @@ long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void
     if (p->smoother == LQ_SMOOTH_GMRES) {
         Exec e = c->ex();
         zero(e, q, z);
-        KResult r = gmres(c, q, v, z, p->smooth_m, p->smooth_n, p->smooth_tol, true, "inner");
+        KResult r = gmres(c, q, v, z, p->smooth_m, p->smooth_n, p->smooth_tol, true, "inner", -1.0, false);
         return r.iters;
     }
     copy(c->ex(), q, v, z);
@@ -658,8 +664,9 @@ long long smoother_schur(lq_ctx *c, const lq_solver_params *p, int q, const void
 // smoother in inner_prec.  Stops at ||b - D_S x|| <= tol * bnorm_ref (bnorm_ref < 0:
 // the norm of b itself).
 KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, long long *inner_iters,
-               double bnorm_ref = -1.0)
+               double bnorm_ref = -1.0, bool confirm = true, int max_cycles = -1)
 {
+    if (max_cycles < 0) max_cycles = p->max_restarts;
     Exec e = c->ex();
     KResult R;
     const int m = p->restart;
@@ -678,7 +685,7 @@ KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lon
         return R;
     }
     Hess H(m);
-    for (int cyc = 0; cyc < p->max_restarts; cyc++) {
+    for (int cyc = 0; cyc < max_cycles; cyc++) {
         void *v0 = vec_at(c, W, V, 0);
         op_schur(c, W, x, v0, t);
         axpby(e, W, 1.0, 0.0, b, -1.0, 0.0, v0);
@@ -721,6 +728,10 @@ KResult fgmres(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lon
         upload_coef(c, y);
         multi_axpy(e, W, Z, nk, c->d_coef, +1, x, nullptr, 0);
         ck_launch(c, "fgmres update");
+        if (!confirm && R.relres <= p->tol) {   // the estimate reached the tolerance: the caller checks
+            R.converged = true;
+            return R;
+        }
     }
     void *r = vec_at(c, W, V, 0);
     op_schur(c, W, x, r, t);
@@ -1337,6 +1348,7 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
         c->red.maxv = RED_SLOTS;
         c->red.partial = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS * c->red.blocks);
         c->red.out = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
+        c->red.ticket = (unsigned *)dev_alloc(c, sizeof(unsigned));
         c->d_coef = (double *)dev_alloc(c, sizeof(double) * 2 * RED_SLOTS);
         c->d_s2 = (double *)dev_alloc(c, sizeof(double) * RED_SLOTS);
         c->dflag = (int *)dev_alloc(c, sizeof(int));
@@ -1584,43 +1596,62 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
         ck_launch(c, "norm of b");
         const double *hb = fetch(c, 0, 2);
         const double bfull = std::sqrt(hb[0] + hb[2]);
+        // The Krylov solver returns once its least-squares estimate reaches the
+        // tolerance; the check is the full system's residual recomputed after
+        // the reconstruction (which is also the reported true residual).  Should
+        // it miss the tolerance, the solve resumes from the current x_e.
+        void *ye = field(c, W, "sol:ye"), *yo = field(c, W, "sol:yo");
         KResult R;
         long long inner = 0;
-        if (p->solver == LQ_SOLVER_GMRES) {
-            if (p->prec != LQ_F32) {
-                R = gmres(c, W, bh, xe, p->restart, p->max_restarts, p->tol, false, "outerV", bfull);
+        int cycles_left = p->max_restarts;
+        bool conv = false, est_conv = false;
+        double rel_true = 0.0;
+        for (;;) {
+            KResult r;
+            if (p->solver == LQ_SOLVER_GMRES) {
+                if (p->prec != LQ_F32) {
+                    r = gmres(c, W, bh, xe, p->restart, cycles_left, p->tol, false, "outerV", bfull, false);
+                } else {
+                    void *bq = field(c, P32, "sol:bq"), *xq = field(c, P32, "sol:xq");
+                    convert(e, W, bh, P32, bq);
+                    convert(e, W, xe, P32, xq);
+                    r = gmres(c, P32, bq, xq, p->restart, cycles_left, p->tol, false, "outerV", bfull, false);
+                    convert(e, P32, xq, W, xe);
+                }
             } else {
-                void *bq = field(c, P32, "sol:bq"), *xq = field(c, P32, "sol:xq");
-                convert(e, W, bh, P32, bq);
-                convert(e, W, xe, P32, xq);
-                R = gmres(c, P32, bq, xq, p->restart, p->max_restarts, p->tol, false, "outerV", bfull);
-                convert(e, P32, xq, W, xe);
+                r = fgmres(c, p, bh, xe, &inner, bfull, false, cycles_left);
             }
-        } else {
-            R = fgmres(c, p, bh, xe, &inner, bfull);
+            R.cycles += r.cycles;
+            R.iters += r.iters;
+            R.relres = r.relres;
+            est_conv = r.converged;
+            cycles_left -= r.cycles;
+            op_reconstruct(c, W, bo, xe, xo);
+            // true residual on the full lattice, in W
+            op_full(c, W, xe, xo, ye, yo);
+            axpby(e, W, 1.0, 0.0, be, -1.0, 0.0, ye);
+            axpby(e, W, 1.0, 0.0, bo, -1.0, 0.0, yo);
+            norm2(e, W, ye, c->red, 0);
+            norm2(e, W, yo, c->red, 1);
+            reduce_finish(e, c->red, 0, 2);
+            ck_launch(c, "true residual");
+            const double *hv = fetch(c, 0, 2);
+            rel_true = bfull > 0 ? std::sqrt(hv[0] + hv[2]) / bfull : 0.0;
+            if (!std::isfinite(rel_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in the true residual");
+            conv = rel_true <= p->tol;
+            // stop when converged, when the solver ran out of cycles without reaching
+            // the tolerance, or when it can make no progress
+            if (conv || !r.converged || cycles_left <= 0 || r.cycles == 0) break;
         }
-        op_reconstruct(c, W, bo, xe, xo);
         export_full(e, W, xe, xo, x);
-        // true residual on the full lattice, in W
-        void *ye = field(c, W, "sol:ye"), *yo = field(c, W, "sol:yo");
-        op_full(c, W, xe, xo, ye, yo);
-        axpby(e, W, 1.0, 0.0, be, -1.0, 0.0, ye);
-        axpby(e, W, 1.0, 0.0, bo, -1.0, 0.0, yo);
-        norm2(e, W, ye, c->red, 0);
-        norm2(e, W, yo, c->red, 1);
-        norm2(e, W, be, c->red, 2);
-        norm2(e, W, bo, c->red, 3);
-        reduce_finish(e, c->red, 0, 4);
-        ck_launch(c, "true residual");
-        const double *hv = fetch(c, 0, 4);
-        const double bn = hv[4] + hv[6];
-        st.rel_resid_true = bn > 0 ? std::sqrt((hv[0] + hv[2]) / bn) : 0.0;
+        st.rel_resid_true = rel_true;
         st.cycles = R.cycles;
         st.iters = R.iters;
         st.inner_iters = inner;
-        st.rel_resid = R.relres;
-        if (!std::isfinite(st.rel_resid_true)) fail(c, LQ_ERR_NAN, "NaN/Inf in the true residual");
-        not_conv = !R.converged;
+        // the Schur residual: recomputed by a solver that ran out of cycles; after a
+        // stop on the estimate it equals the full residual just computed
+        st.rel_resid = est_conv ? rel_true : R.relres;
+        not_conv = !conv;
     });
     if (c) {
         st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -151,6 +151,73 @@ __global__ void __launch_bounds__(RT, 4) multi_axpy_kernel(const typename Vec<R>
     }
 }
 
+// multi_axpy_finish (FP32): see lq_kernels.h
+__global__ void __launch_bounds__(RT, 4) multi_axpy_fin_kernel(const float4 *__restrict__ Vb, long long n, int nv,
+                                                               double *partial, int pitch,
+                                                               const double *__restrict__ scale, float sign,
+                                                               float4 *y, int nrm_slot, double *out,
+                                                               unsigned *ticket)
+{
+    __shared__ double cd[512];
+    __shared__ float csr[256], csi[256];
+    __shared__ double shd[RT / 32];
+    __shared__ float shf[RT / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // finish the dot products: warp w takes values w, w + 8, ..., each lane the
+    // blocks lane, lane + 32, ... in order, then a fixed shuffle tree
+    for (int v = warp; v < 2 * nv; v += RT / 32) {
+        double a = 0.0;
+        for (int b = lane; b < gridDim.x; b += 32) a += __ldcg(partial + (long long)b * pitch + v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) cd[v] = scale ? a * scale[v >> 1] : a;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nv; j += RT) {
+        csr[j] = sign * (float)cd[2 * j];
+        csi[j] = sign * (float)cd[2 * j + 1];
+        if (blockIdx.x == 0) {
+            out[2 * j] = cd[2 * j];
+            out[2 * j + 1] = cd[2 * j + 1];
+        }
+    }
+    __syncthreads();
+    float nrm[1] = {0.0f};
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        float4 yv = y[i];
+        int j = 0;
+        for (; j + 4 <= nv; j += 4) {
+            float4 vv[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) vv[q] = __ldg(Vb + (j + q) * n + i);
+#pragma unroll
+            for (int q = 0; q < 4; q++) caxpy(csr[j + q], csi[j + q], vv[q], yv);
+        }
+        for (; j < nv; j++) caxpy(csr[j], csi[j], __ldg(Vb + j * n + i), yv);
+        y[i] = yv;
+        nrm[0] = nrm_acc(yv, nrm[0]);
+    }
+    block_sum<float, 1>(nrm, shf);
+    if (threadIdx.x == 0) {   // the norm partials share the dot partials' array (slot nrm_slot)
+        partial[(long long)blockIdx.x * pitch + 2 * nrm_slot] = (double)nrm[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {   // the last block to finish sums the norm partials in a fixed order
+        __threadfence();
+        double a[1] = {0.0};
+        for (int b = threadIdx.x; b < gridDim.x; b += RT) a[0] += __ldcg(partial + (long long)b * pitch + 2 * nrm_slot);
+        block_sum<double, 1>(a, shd);
+        if (threadIdx.x == 0) {
+            out[2 * nrm_slot] = a[0];
+            out[2 * nrm_slot + 1] = 0.0;
+            *ticket = 0u;
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(RT) norm2_kernel(const typename Vec<R>::V *__restrict__ w, long long n,
                                                    double *partial, int pitch, int slot)
@@ -382,6 +449,15 @@ void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_
             multi_axpy_kernel<float, false><<<blocks, RT, 0, e.st>>>((const float4 *)V, n, nv, c, (float)sign,
                                                                      (float4 *)y, part, pitch, slot);
     }
+}
+
+void multi_axpy_finish(const Exec &e, const void *V, int nv, const RedScratch &r, const double *scale, int sign,
+                       void *y, int nrm_slot)
+{
+    Launch L_(e, K_AXPY_F32, (double)e.g.Vh * sp_bytes(P32) * (nv + 2), (double)e.g.Vh * 96 * nv);
+    const int blocks = reduction_blocks(e.g);   // the multi-dot's grid: one partial per block
+    multi_axpy_fin_kernel<<<blocks, RT, 0, e.st>>>((const float4 *)V, nvec(e.g, P32), nv, r.partial, 2 * r.maxv,
+                                                   scale, (float)sign, (float4 *)y, nrm_slot, r.out, r.ticket);
 }
 
 template <typename R, int NJ>
