@@ -431,8 +431,8 @@ double arnoldi_scaled(lq_ctx *c, void *V, int k, void *w, Hess &H, double *s)
 {
     Exec e = c->ex();
     const int n = k + 1;
-    multi_dot(e, P32, V, n, w, c->red, 0);
-    multi_axpy_finish(e, V, n, c->red, c->d_s2, -1, w, n);   // finishes the dots and the new norm itself
+    multi_dot_finish(e, V, n, w, c->red, c->d_s2);   // s_j^2 (V_j, w) into red.out
+    multi_axpy_finish(e, V, n, c->red, -1, w, n);    // w -= sum_j ..., ||w||^2 into red.out[n]
     ck_launch(c, "arnoldi");
     const double *hv = fetch(c, 0, n + 1);
     for (int j = 0; j < n; j++) H.h(j, k) = cd(hv[2 * j], hv[2 * j + 1]) * (s[k] / s[j]);

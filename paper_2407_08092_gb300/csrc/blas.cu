@@ -89,11 +89,41 @@ __device__ __forceinline__ void block_sum(A v[N], A *sh /* [RT/32][N] */)
     __syncthreads();
 }
 
+// The last block of a launch to finish (counted on `ticket`, which it resets to
+// zero) sums the blocks' partials of `nval` values from value index v0 in a
+// fixed order (warp w takes values w, w + 8, ..., each lane the blocks lane,
+// lane + 32, ...), scales value v by scale[v / 2] when a scale is given, and
+// writes them to out[v]: a deterministic second stage without a second launch.
+__device__ __forceinline__ void last_block_finish(double *partial, int pitch, int v0, int nval,
+                                                  const double *scale, double *out, unsigned *ticket)
+{
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = v0 + warp; v < v0 + nval; v += RT / 32) {
+        double a = 0.0;
+        for (int b = lane; b < gridDim.x; b += 32) a += __ldcg(partial + (long long)b * pitch + v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[v] = scale ? a * scale[v >> 1] : a;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // ---- multi-dot: partial[blk][2*(slot0+j) + re/im] = block share of (v_j, w) ------
-template <typename R, int NJ>
+// (FIN: the last block also finishes the launch's values into out)
+template <typename R, int NJ, bool FIN = false>
 __global__ void __launch_bounds__(RT, 4) multi_dot_kernel(const typename Vec<R>::V *__restrict__ Vb, long long n,
                                                           const typename Vec<R>::V *__restrict__ w, double *partial,
-                                                          int pitch, int slot0)
+                                                          int pitch, int slot0, const double *scale = nullptr,
+                                                          double *out = nullptr, unsigned *ticket = nullptr)
 {
     __shared__ R sh[(RT / 32) * 2 * NJ];
     R acc[2 * NJ];
@@ -108,6 +138,7 @@ __global__ void __launch_bounds__(RT, 4) multi_dot_kernel(const typename Vec<R>:
     if (threadIdx.x == 0)
 #pragma unroll
         for (int j = 0; j < 2 * NJ; j++) partial[(long long)blockIdx.x * pitch + 2 * slot0 + j] = (double)acc[j];
+    if (FIN) last_block_finish(partial, pitch, 2 * slot0, 2 * NJ, scale, out, ticket);
 }
 
 // ---- y = y + sign * sum_j c_j v_j, optionally the partials of ||y_new||^2 ------------
@@ -153,34 +184,16 @@ __global__ void __launch_bounds__(RT, 4) multi_axpy_kernel(const typename Vec<R>
 
 // multi_axpy_finish (FP32): see lq_kernels.h
 __global__ void __launch_bounds__(RT, 4) multi_axpy_fin_kernel(const float4 *__restrict__ Vb, long long n, int nv,
-                                                               double *partial, int pitch,
-                                                               const double *__restrict__ scale, float sign,
-                                                               float4 *y, int nrm_slot, double *out,
+                                                               const double *c, float sign, float4 *y,
+                                                               double *partial, int pitch, int nrm_slot, double *out,
                                                                unsigned *ticket)
 {
-    __shared__ double cd[512];
+    __shared__ float sh[RT / 32];
     __shared__ float csr[256], csi[256];
-    __shared__ double shd[RT / 32];
-    __shared__ float shf[RT / 32];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // finish the dot products: warp w takes values w, w + 8, ..., each lane the
-    // blocks lane, lane + 32, ... in order, then a fixed shuffle tree
-    for (int v = warp; v < 2 * nv; v += RT / 32) {
-        double a = 0.0;
-        for (int b = lane; b < gridDim.x; b += 32) a += __ldcg(partial + (long long)b * pitch + v);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) cd[v] = scale ? a * scale[v >> 1] : a;
-    }
-    __syncthreads();
     for (int j = threadIdx.x; j < nv; j += RT) {
-        csr[j] = sign * (float)cd[2 * j];
-        csi[j] = sign * (float)cd[2 * j + 1];
-        if (blockIdx.x == 0) {
-            out[2 * j] = cd[2 * j];
-            out[2 * j + 1] = cd[2 * j + 1];
-        }
+        const double2 cj = reinterpret_cast<const double2 *>(c)[j];
+        csr[j] = sign * (float)cj.x;
+        csi[j] = sign * (float)cj.y;
     }
     __syncthreads();
     float nrm[1] = {0.0f};
@@ -198,24 +211,12 @@ __global__ void __launch_bounds__(RT, 4) multi_axpy_fin_kernel(const float4 *__r
         y[i] = yv;
         nrm[0] = nrm_acc(yv, nrm[0]);
     }
-    block_sum<float, 1>(nrm, shf);
-    if (threadIdx.x == 0) {   // the norm partials share the dot partials' array (slot nrm_slot)
+    block_sum<float, 1>(nrm, sh);
+    if (threadIdx.x == 0) {
         partial[(long long)blockIdx.x * pitch + 2 * nrm_slot] = (double)nrm[0];
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        partial[(long long)blockIdx.x * pitch + 2 * nrm_slot + 1] = 0.0;
     }
-    __syncthreads();
-    if (last) {   // the last block to finish sums the norm partials in a fixed order
-        __threadfence();
-        double a[1] = {0.0};
-        for (int b = threadIdx.x; b < gridDim.x; b += RT) a[0] += __ldcg(partial + (long long)b * pitch + 2 * nrm_slot);
-        block_sum<double, 1>(a, shd);
-        if (threadIdx.x == 0) {
-            out[2 * nrm_slot] = a[0];
-            out[2 * nrm_slot + 1] = 0.0;
-            *ticket = 0u;
-        }
-    }
+    last_block_finish(partial, pitch, 2 * nrm_slot, 2, nullptr, out, ticket);
 }
 
 template <typename R>
@@ -451,13 +452,41 @@ void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_
     }
 }
 
-void multi_axpy_finish(const Exec &e, const void *V, int nv, const RedScratch &r, const double *scale, int sign,
-                       void *y, int nrm_slot)
+void multi_axpy_finish(const Exec &e, const void *V, int nv, const RedScratch &r, int sign, void *y, int nrm_slot)
 {
     Launch L_(e, K_AXPY_F32, (double)e.g.Vh * sp_bytes(P32) * (nv + 2), (double)e.g.Vh * 96 * nv);
-    const int blocks = reduction_blocks(e.g);   // the multi-dot's grid: one partial per block
-    multi_axpy_fin_kernel<<<blocks, RT, 0, e.st>>>((const float4 *)V, nvec(e.g, P32), nv, r.partial, 2 * r.maxv,
-                                                   scale, (float)sign, (float4 *)y, nrm_slot, r.out, r.ticket);
+    const int blocks = reduction_blocks(e.g);
+    multi_axpy_fin_kernel<<<blocks, RT, 0, e.st>>>((const float4 *)V, nvec(e.g, P32), nv, r.out, (float)sign,
+                                                   (float4 *)y, r.partial, 2 * r.maxv, nrm_slot, r.out, r.ticket);
+}
+
+template <int NJ>
+static void dot_fin_launch(const Exec &e, const RedScratch &r, const void *V, long long n, const void *w, int slot0,
+                           const double *scale)
+{
+    multi_dot_kernel<float, NJ, true><<<r.blocks, RT, 0, e.st>>>((const float4 *)V, n, (const float4 *)w, r.partial,
+                                                                 2 * r.maxv, slot0, scale, r.out, r.ticket);
+}
+
+void multi_dot_finish(const Exec &e, const void *V, int nv, const void *w, const RedScratch &r, const double *scale)
+{
+    const long long n = nvec(e.g, P32);
+    const size_t vb = spinor_bytes(e.g, P32);
+    for (int j0 = 0; j0 < nv; j0 += MAXJ) {
+        const int nj = nv - j0 < MAXJ ? nv - j0 : MAXJ;
+        Launch L_(e, K_DOT_F32, (double)e.g.Vh * sp_bytes(P32) * (nj + 1), (double)e.g.Vh * 96 * nj);
+        const void *Vj = (const char *)V + (size_t)j0 * vb;
+        switch (nj) {
+        case 1: dot_fin_launch<1>(e, r, Vj, n, w, j0, scale); break;
+        case 2: dot_fin_launch<2>(e, r, Vj, n, w, j0, scale); break;
+        case 3: dot_fin_launch<3>(e, r, Vj, n, w, j0, scale); break;
+        case 4: dot_fin_launch<4>(e, r, Vj, n, w, j0, scale); break;
+        case 5: dot_fin_launch<5>(e, r, Vj, n, w, j0, scale); break;
+        case 6: dot_fin_launch<6>(e, r, Vj, n, w, j0, scale); break;
+        case 7: dot_fin_launch<7>(e, r, Vj, n, w, j0, scale); break;
+        default: dot_fin_launch<8>(e, r, Vj, n, w, j0, scale); break;
+        }
+    }
 }
 
 template <typename R, int NJ>

@@ -230,14 +230,13 @@ struct RedScratch {
 // partials of ||y_new||^2 into slot `slot`
 void multi_axpy(const Exec &e, int prec, const void *V, int nv, const double *c_dev, int sign,
                 void *y, const RedScratch *r, int slot);
-// FP32: y = y + sign * sum_j c_j v_j where c_j = scale_j * (v_j, y) is finished
-// here from the multi-dot partials in slots 0 .. nv-1 (every block sums them in
-// the same fixed order; block 0 stores c_j in r.out[j]), and ||y_new||^2 into
-// r.out[nrm_slot], summed from the blocks' partials by the last block to finish:
-// the Arnoldi step of the unnormalised FP32 basis in one launch after the
-// multi-dot, without the two separate reduce_finish launches
-void multi_axpy_finish(const Exec &e, const void *V, int nv, const RedScratch &r, const double *scale, int sign,
-                       void *y, int nrm_slot);
+// FP32 pair of the Arnoldi step on the unnormalised basis, with no separate
+// reduction launches: multi_dot_finish writes scale_j * (v_j, w) for j < nv to
+// r.out slots 0 .. nv-1 (the last block of each launch sums the partials in a
+// fixed order); multi_axpy_finish then forms y = y + sign * sum_j r.out_j v_j and
+// writes ||y_new||^2 to r.out slot nrm_slot (summed the same way by its last block)
+void multi_dot_finish(const Exec &e, const void *V, int nv, const void *w, const RedScratch &r, const double *scale);
+void multi_axpy_finish(const Exec &e, const void *V, int nv, const RedScratch &r, int sign, void *y, int nrm_slot);
 // partials of (v_j, w) = sum conj(v_j) w for j < nv into slots slot0 + j
 void multi_dot(const Exec &e, int prec, const void *V, int nv, const void *w, const RedScratch &r,
                int slot0);
