@@ -35,6 +35,8 @@
  * Errors.  Every call returns an lq_status; nothing aborts, traps or throws
  *   across this boundary.  lq_last_error() describes the most recent failure
  *   of a context.  A failed call leaves output buffers unspecified.
+ * Tracing.  Every call that launches work opens an NVTX range named after the
+ *   call (visible in profiler timelines; without a profiler it costs nothing).
  * Ownership.  The library owns the context, its internal field copies and
  *   the Krylov workspace (allocated on first use, sized by the restart
  *   length, freed by lq_destroy).  The caller owns every buffer it passes.

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/lqdd.h"
+#include <nvtx3/nvToolsExt.h>
 #include "lq_kernels.h"
 
 using namespace lq;
@@ -83,6 +84,13 @@ cudaEvent_t Prof::get()
     return pool[next++];
 }
 }  // namespace lq
+
+// An NVTX range around one C-ABI call, so that profiler timelines show which
+// call each kernel belongs to (header-only NVTX: a no-op without a profiler).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 namespace {
 
@@ -1377,6 +1385,7 @@ lq_status lq_destroy(lq_ctx *c)
 
 lq_status lq_set_gauge(lq_ctx *c, const void *U)
 {
+    const NvtxRange range_("lq_set_gauge");
     return guarded(c, [&] {
         if (!U) fail(c, LQ_ERR_ARG, "U is NULL");
         Exec e = c->ex();
@@ -1420,6 +1429,7 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
 
 lq_status lq_apply(lq_ctx *c, int op, int prec, const void *in, void *out)
 {
+    const NvtxRange range_("lq_apply");
     return guarded(c, [&] {
         if (!in || !out) fail(c, LQ_ERR_ARG, "NULL field");
         if (!valid_prec(prec) && prec != LQ_BF16) fail(c, LQ_ERR_ARG, "bad precision");
@@ -1465,6 +1475,7 @@ lq_status lq_apply(lq_ctx *c, int op, int prec, const void *in, void *out)
 
 lq_status lq_prepare(lq_ctx *c, const void *b, void *bhat_e)
 {
+    const NvtxRange range_("lq_prepare");
     return guarded(c, [&] {
         if (!b || !bhat_e) fail(c, LQ_ERR_ARG, "NULL field");
         need_gauge(c);
@@ -1479,6 +1490,7 @@ lq_status lq_prepare(lq_ctx *c, const void *b, void *bhat_e)
 
 lq_status lq_reconstruct(lq_ctx *c, const void *b, const void *x_e, void *x)
 {
+    const NvtxRange range_("lq_reconstruct");
     return guarded(c, [&] {
         if (!b || !x_e || !x) fail(c, LQ_ERR_ARG, "NULL field");
         need_gauge(c);
@@ -1494,6 +1506,7 @@ lq_status lq_reconstruct(lq_ctx *c, const void *b, const void *x_e, void *x)
 
 lq_status lq_estimate_norm(lq_ctx *c, int prec, int iters, const void *v0, double *out)
 {
+    const NvtxRange range_("lq_estimate_norm");
     return guarded(c, [&] {
         if (!v0 || !out || iters < 1) fail(c, LQ_ERR_ARG, "bad argument");
         if (!valid_prec(prec)) fail(c, LQ_ERR_ARG, "bad precision");
@@ -1521,6 +1534,7 @@ lq_status lq_estimate_norm(lq_ctx *c, int prec, int iters, const void *v0, doubl
 
 lq_status lq_norm2(lq_ctx *c, const void *v, long long n_sites, double *out)
 {
+    const NvtxRange range_("lq_norm2");
     return guarded(c, [&] {
         if (!v || !out || n_sites < 0) fail(c, LQ_ERR_ARG, "bad argument");
         Exec e = c->ex();
@@ -1533,6 +1547,7 @@ lq_status lq_norm2(lq_ctx *c, const void *v, long long n_sites, double *out)
 
 lq_status lq_smooth(lq_ctx *c, const lq_solver_params *p, const void *r, void *eo)
 {
+    const NvtxRange range_("lq_smooth");
     return guarded(c, [&] {
         if (!r || !eo) fail(c, LQ_ERR_ARG, "NULL field");
         check_params(c, p, false);
@@ -1569,6 +1584,7 @@ lq_status lq_smooth(lq_ctx *c, const lq_solver_params *p, const void *r, void *e
 
 lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x, lq_stats *stats)
 {
+    const NvtxRange range_("lq_solve");
     bool not_conv = false;
     auto t0 = std::chrono::steady_clock::now();
     const long long l0 = c ? c->ctr.launches : 0;
@@ -1753,6 +1769,7 @@ lq_status lq_group_tuning(lq_group *G, int *sites_per_tile, int *rhs_per_thread,
 lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rhs, const void *const *b,
                          void *const *x, lq_stats *stats)
 {
+    const NvtxRange range_("lq_solve_group");
     if (!G) return LQ_ERR_ARG;
     lq_ctx *c = gctx(G);
     const int M = (int)G->mem.size();
@@ -1953,6 +1970,7 @@ lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rh
 
 lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const void *b, void *x, lq_stats *stats)
 {
+    const NvtxRange range_("lq_solve_batch");
     if (!c) return LQ_ERR_ARG;
     if (!c->self_group) {
         lq_ctx *one[1] = {c};
@@ -1967,6 +1985,7 @@ lq_status lq_solve_batch(lq_ctx *c, const lq_solver_params *p, int n_rhs, const 
 
 lq_status lq_export_clover(lq_ctx *c, int which, void *out)
 {
+    const NvtxRange range_("lq_export_clover");
     return guarded(c, [&] {
         if (!out || (which != 0 && which != 1)) fail(c, LQ_ERR_ARG, "bad argument");
         need_gauge(c);
@@ -1995,6 +2014,7 @@ static void force_apply(lq_ctx *c, const void *X, const void *Y, double coef, vo
 
 lq_status lq_force(lq_ctx *c, const void *X, const void *Y, double coef, void *G)
 {
+    const NvtxRange range_("lq_force");
     return guarded(c, [&] {
         if (!X || !Y || !G) fail(c, LQ_ERR_ARG, "NULL field");
         need_gauge(c);
@@ -2033,6 +2053,7 @@ static lq_status action_solves(lq_ctx *c, const lq_solver_params *p, const void 
 lq_status lq_fermion_action(lq_ctx *c, const lq_solver_params *p, const void *phi, void *X, void *Y, double *S,
                             lq_stats *stats)
 {
+    const NvtxRange range_("lq_fermion_action");
     lq_stats st[2] = {};
     bool not_conv = false;
     const lq_status s = action_solves(c, p, phi, X, Y, S, st, &not_conv);
@@ -2050,6 +2071,7 @@ lq_status lq_fermion_action(lq_ctx *c, const lq_solver_params *p, const void *ph
 lq_status lq_fermion_force(lq_ctx *c, const lq_solver_params *p, const void *phi, double *S, void *G,
                            lq_stats *stats)
 {
+    const NvtxRange range_("lq_fermion_force");
     lq_stats st[2] = {};
     bool not_conv = false;
     lq_status s = guarded(c, [&] {
