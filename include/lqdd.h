@@ -141,11 +141,12 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream);
 lq_status lq_destroy(lq_ctx *ctx);
 
 /* Load a gauge field (device U[V][4][3][3], complex double, natural order) and
- * build from it, on the device: the internal FP64, FP32 and df64 link copies,
- * the clover term C(x) of every site (Sec. 2.3) and the inverse D_oo^{-1} of
- * the odd blocks (6x6 Hermitian blocks, Sec. 2.4.5), both in df64 and FP32.
- * The FP64 clover copies and the BF16 links are rounded from these when an
- * FP64 or BF16 operator (or lq_export_clover) first needs them after the call.
+ * build from it, on the device: the internal df64 and FP32 link copies, the
+ * clover term C(x) of every site (Sec. 2.3) and the inverse D_oo^{-1} of the odd
+ * blocks (6x6 Hermitian blocks, Sec. 2.4.5), both in df64 and FP32.  The FP64
+ * links and clover blocks (hi + lo of the df64 copies, about 48 significand
+ * bits) and the BF16 links are rounded from these when an FP64 or BF16
+ * operator (or lq_export_clover) first needs them after the call.
  * Links are expected to be SU(3); the FP32 and BF16 copies keep two rows and
  * rebuild the third as conj(r1 x r2).  The caller's U may be freed on return.
  * Synchronises; LQ_ERR_BREAKDOWN if a clover block has a non-positive pivot. */

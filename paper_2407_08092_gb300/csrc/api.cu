@@ -47,6 +47,7 @@ struct lq_ctx {
     bool have_gauge = false;
     bool clover64 = false;            // C64 / Ci64 rounded from the current df64 blocks
     bool links16 = false;             // U16 rounded from the current FP32 links
+    bool links64 = false;             // U64 rounded from the current df64 links
     void *U64[2] = {nullptr, nullptr};
     void *U32[2] = {nullptr, nullptr};
     void *C64[2] = {nullptr, nullptr};
@@ -185,9 +186,10 @@ void need_gauge(lq_ctx *c)
     if (!c->have_gauge) fail(c, LQ_ERR_STATE, "no gauge field: call lq_set_gauge first");
 }
 
-// The FP64 clover blocks and the BF16 links are rounded copies that only the
-// FP64 operator and the BF16 hops read: they are made on first use after each
-// lq_set_gauge, on the context's stream.
+// The FP64 clover blocks and links and the BF16 links are rounded copies that
+// only the FP64 operator and the BF16 hops read: they are made on first use
+// after each lq_set_gauge, on the context's stream.  The FP64 copies are
+// hi + lo of the df64 ones (about 48 significand bits of the caller's field).
 void need_clover64(lq_ctx *c)
 {
     if (c->clover64) return;
@@ -195,6 +197,13 @@ void need_clover64(lq_ctx *c)
     for (int p = 0; p < 2; p++) clover_to_f64(e, c->Cdf[p], c->C64[p]);
     clover_to_f64(e, c->Cidf, c->Ci64);
     c->clover64 = true;
+}
+void need_links64(lq_ctx *c)
+{
+    if (c->links64) return;
+    Exec e = c->ex();
+    for (int p = 0; p < 2; p++) df64_to_f64(e, c->Udf[p], c->U64[p], 36LL * c->g.stride);
+    c->links64 = true;
 }
 void need_links16(lq_ctx *c)
 {
@@ -224,6 +233,7 @@ HopCall hopcall(lq_ctx *c, int mode, int prec, int pout)
     h.prec = prec;
     h.pout = pout;
     if (prec == P16) need_links16(c);
+    if (prec == P64) need_links64(c);
     for (int p = 0; p < 2; p++)
         h.U[p] = prec == P64 ? c->U64[p] : prec == P32 ? c->U32[p] : prec == P16 ? c->U16[p] : c->Udf[p];
     return h;
@@ -1409,10 +1419,11 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
         c->have_gauge = false;
         c->clover64 = false;
         c->links16 = false;
-        // links in FP64, FP32 and df64; clover and inverse built in df64, their
-        // FP32 copies rounded by the same kernels (FP64 clover and BF16 links
-        // follow on first use)
-        import_links(e, U, c->U64, c->U32, c->Udf);
+        c->links64 = false;
+        // links in FP32 and df64; clover and inverse built in df64, their FP32
+        // copies rounded by the same kernels (the FP64 links and clover and the
+        // BF16 links follow on first use)
+        import_links(e, U, nullptr, c->U32, c->Udf);
         const void *udf[2] = {c->Udf[0], c->Udf[1]};
         clover_build(e, udf, c->lat.csw, c->lat.m0, c->Cdf, c->C32, ws(c, "clover:F", (size_t)6 * 9 * 8 * g.V),
                      ws(c, "clover:R", (size_t)6 * 9 * 8 * g.V));

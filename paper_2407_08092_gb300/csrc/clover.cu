@@ -459,6 +459,12 @@ void clover_to_f64(const Exec &e, const void *Cdf, void *C64)
     clover_f64_kernel<<<blocks_for(n, 256), 256, 0, e.st>>>(n, (const df2 *)Cdf, (double2 *)C64);
 }
 
+void df64_to_f64(const Exec &e, const void *in, void *out, long long n)
+{
+    Launch L_(e, K_LAYOUT, (double)n * 32);
+    clover_f64_kernel<<<blocks_for(n, 256), 256, 0, e.st>>>(n, (const df2 *)in, (double2 *)out);
+}
+
 void clover_export(const Exec &e, const void *Ce, const void *Co, void *out)
 {
     Launch L_(e, K_CLOVER, (double)e.g.V * (72 * 8 + 72 * 16));

@@ -155,43 +155,53 @@ __global__ void __launch_bounds__(TT) import_links_kernel(Geom g, const double2 
                                                           double2 *U64o, float4 *U32e, float4 *U32o, df2 *Udfe,
                                                           df2 *Udfo)
 {
+    // tile rows are stored de-interleaved, row r at slot (r & 1) * TL/2 + r / 2, so
+    // that the rows 2j + b that consecutive j read below sit in consecutive slots
+    // (distinct shared-memory banks) whatever b
     __shared__ double2 tile[TL][LPAD];
     __shared__ unsigned char par[TL / 2];
     const long long r0 = (long long)blockIdx.x * TL;
     const int rows = (int)(g.V - r0 < TL ? g.V - r0 : TL);
-    for (int i = threadIdx.x; i < rows * 36; i += TT) tile[i / 36][i % 36] = __ldg(U + r0 * 36 + i);
+    for (int i = threadIdx.x; i < rows * 36; i += TT) {
+        const int r = i / 36;
+        tile[(r & 1) * (TL / 2) + (r >> 1)][i % 36] = __ldg(U + r0 * 36 + i);
+    }
     if (threadIdx.x < TL / 2 && 2 * (int)threadIdx.x < rows) par[threadIdx.x] = lex_parity(g, r0 + 2 * threadIdx.x);
     __syncthreads();
     const long long s0 = r0 / 2;
-    // 36 complex entries of FP64 and df64 per site, then 12 float4 of FP32
+    // entry k = mu * 9 + e of link mu: its FP64 copy (only when asked for), its
+    // df64 split, and for the first two rows (e < 6) the FP32 value, which is the
+    // split's high part: the half (e & 1) of float4 mu * 3 + e / 2 of the
+    // 12-real FP32 link
     auto put = [&](int j, int pk) {
-        const int p = pk / 48, k = pk % 48;
-        const double2 *row = tile[LQ_IDX(tile_row<true>(par, j, p), rows, B_LAYOUT)];
+        const int p = pk / 36, k = pk % 36;
+        const int r = (int)LQ_IDX(tile_row<true>(par, j, p), rows, B_LAYOUT);
+        const double2 *row = tile[(r & 1) * (TL / 2) + (r >> 1)];
         const long long s = LQ_IDX(s0 + j, g.Vh, B_LAYOUT);
-        if (k < 36) {   // k = mu * 9 + entry
-            (p ? U64o : U64e)[k * g.stride + s] = row[k];
-            (p ? Udfo : Udfe)[k * g.stride + s] = to_df2(row[k]);
-        } else {        // k - 36 = mu * 3 + v: entries 2v, 2v + 1 of link mu
-            const int mu = (k - 36) / 3, v = (k - 36) % 3;
-            const double2 a = row[mu * 9 + 2 * v], b = row[mu * 9 + 2 * v + 1];
-            (p ? U32o : U32e)[(k - 36) * g.stride + s] =
-                make_float4(d2f_bits(a.x), d2f_bits(a.y), d2f_bits(b.x), d2f_bits(b.y));
+        if (U64e) (p ? U64o : U64e)[k * g.stride + s] = row[k];
+        const df2 d = to_df2(row[k]);
+        (p ? Udfo : Udfe)[k * g.stride + s] = d;
+        const int mu = k / 9, e = k % 9;
+        if (e < 6) {
+            float2 *f = reinterpret_cast<float2 *>(p ? U32o : U32e);
+            f[((mu * 3 + e / 2) * g.stride + s) * 2 + (e & 1)] = make_float2(d.rh, d.ih);
         }
     };
     if (rows == TL) {   // a whole tile: w splits by constants
-        for (int w = threadIdx.x; w < 2 * 48 * (TL / 2); w += TT) put(w % (TL / 2), w / (TL / 2));
+        for (int w = threadIdx.x; w < 2 * 36 * (TL / 2); w += TT) put(w % (TL / 2), w / (TL / 2));
     } else {
         const int per = rows / 2;
-        for (int w = threadIdx.x; w < 2 * 48 * per; w += TT) put(w % per, w / per);
+        for (int w = threadIdx.x; w < 2 * 36 * per; w += TT) put(w % per, w / per);
     }
 }
 
 void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2], void *Udf[2])
 {
-    Launch L_(e, K_LAYOUT, (double)e.g.V * 4 * (144 + 144 + 48 + 144));
-    import_links_kernel<<<nblk(e.g.V, TL), TT, 0, e.st>>>(e.g, (const double2 *)U_nat, (double2 *)U64[0],
-                                                          (double2 *)U64[1], (float4 *)U32[0], (float4 *)U32[1],
-                                                          (df2 *)Udf[0], (df2 *)Udf[1]);
+    Launch L_(e, K_LAYOUT, (double)e.g.V * 4 * (144 + (U64 ? 144 : 0) + 48 + 144));
+    import_links_kernel<<<nblk(e.g.V, TL), TT, 0, e.st>>>(e.g, (const double2 *)U_nat,
+                                                          U64 ? (double2 *)U64[0] : nullptr,
+                                                          U64 ? (double2 *)U64[1] : nullptr, (float4 *)U32[0],
+                                                          (float4 *)U32[1], (df2 *)Udf[0], (df2 *)Udf[1]);
 }
 
 // ---- spinors ----------------------------------------------------------------

@@ -82,8 +82,11 @@ inline size_t spinor_bytes(const Geom &g, int prec)
 }
 
 // ---- layout (layout.cu) ----------------------------------------------------
-// natural complex-double gauge field -> per-parity internal link copies
+// natural complex-double gauge field -> per-parity internal link copies (the
+// FP64 ones only when U64 is non-null)
 void import_links(const Exec &e, const void *U_nat, void *U64[2], void *U32[2], void *Udf[2]);
+// out = hi + lo for n df64 complex slots (FP64 copies rounded from df64 ones)
+void df64_to_f64(const Exec &e, const void *in, void *out, long long n);
 // BF16 12-real links of one parity from the FP32 ones
 void links_to_bf16(const Exec &e, const void *U32, void *U16);
 // BF16 fields (bf16.cu): conversions (one side BF16), natural half spinors,
