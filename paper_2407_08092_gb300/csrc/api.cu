@@ -69,6 +69,7 @@ struct lq_ctx {
     Prof prof;
     lq_group *self_group = nullptr;   // the one-member group behind lq_solve_batch
     int sap_b[4] = {0, 0, 0, 0};      // block extents of the SAP origin tables below
+    int sapbm_b[4] = {0, 0, 0, 0};    // block extents of the block-major SAP copies (0: none for this gauge)
     int4 *sap_origin[2] = {nullptr, nullptr};
     int sap_count[2] = {0, 0};
     Exec ex() { return Exec{g, st, &ctr, &prof}; }
@@ -609,12 +610,27 @@ void sap_tables(lq_ctx *c, const int b[4])
     std::copy(b, b + 4, c->sap_b);
 }
 
+// The block-major copies of the FP32 links and clover fields that the SAP
+// block solves read, made on first use for a gauge field and block shape.
+void need_sap_block_major(lq_ctx *c, const int b[4])
+{
+    if (std::equal(b, b + 4, c->sapbm_b)) return;
+    Exec e = c->ex();
+    const size_t lb = (size_t)4 * 3 * c->g.stride * 16, cb = (size_t)2 * 9 * c->g.stride * 16;
+    for (int p = 0; p < 2; p++) {
+        sap_block_major(e, b, p, 12, c->U32[p], ws(c, p ? "sap:Ub1" : "sap:Ub0", lb));
+        sap_block_major(e, b, p, 18, p ? c->Ci32 : c->C32[0], ws(c, p ? "sap:Cb1" : "sap:Cb0", cb));
+    }
+    std::copy(b, b + 4, c->sapbm_b);
+}
+
 // x = SAP(n, m) b from x = 0 on the full lattice, FP32 internal fields
 void sap_apply(lq_ctx *c, const lq_solver_params *p, const void *be, const void *bo, void *xe, void *xo)
 {
     int b[4];
     sap_dims(c, p, b);
     sap_tables(c, b);
+    need_sap_block_major(c, b);
     Exec e = c->ex();
     zero(e, P32, xe);
     zero(e, P32, xo);
@@ -622,8 +638,11 @@ void sap_apply(lq_ctx *c, const lq_solver_params *p, const void *be, const void 
     std::copy(b, b + 4, L.b);
     L.U[0] = c->U32[0];
     L.U[1] = c->U32[1];
-    L.Ce = c->C32[0];
-    L.Ci = c->Ci32;
+    const size_t lb = (size_t)4 * 3 * c->g.stride * 16, cb = (size_t)2 * 9 * c->g.stride * 16;
+    L.Ub[0] = ws(c, "sap:Ub0", lb);
+    L.Ub[1] = ws(c, "sap:Ub1", lb);
+    L.Ce = ws(c, "sap:Cb0", cb);
+    L.Ci = ws(c, "sap:Cb1", cb);
     L.x[0] = xe;
     L.x[1] = xo;
     // the blocks' even residual and each colour's last correction, on the
@@ -1420,6 +1439,7 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
         c->clover64 = false;
         c->links16 = false;
         c->links64 = false;
+        std::fill(c->sapbm_b, c->sapbm_b + 4, 0);
         // links in FP32 and df64; clover and inverse built in df64, their FP32
         // copies rounded by the same kernels (the FP64 links and clover and the
         // BF16 links follow on first use)

@@ -129,9 +129,10 @@ struct SapLaunch {
     int b[4];                 // block extents: even, dividing the lattice, b0 b1 b2 b3 <= 256
     const int4 *origin;       // device: first site of each block of the colour
     int count;                // blocks of the colour
-    const void *U[2];         // FP32 links by parity
-    const void *Ce;           // FP32 C of the even sites
-    const void *Ci;           // FP32 C^{-1} of the odd sites
+    const void *U[2];         // FP32 links by parity, lattice order
+    const void *Ub[2];        // FP32 links by parity, block-major order (sap_block_major)
+    const void *Ce;           // FP32 C of the even sites, block-major order
+    const void *Ci;           // FP32 C^{-1} of the odd sites, block-major order
     const void *rin[2];       // FP32 residual of the blocks before the face update (rin[1] null: zero)
     const void *eface[2];     // FP32 last correction of the other colour (null: none yet)
     void *rout_e;             // FP32 out: the blocks' even residual after the solve
@@ -141,6 +142,11 @@ struct SapLaunch {
     int m;
 };
 void sap_blocks(const Exec &e, const SapLaunch &s);
+// Block-major copy of a parity-`parity` FP32 field of `rows` float4 rows (the
+// links: 12, a clover field: 18) for the blocks with extents b: the blocks in
+// lexicographic order of their block coordinates, each block's sites in its
+// local checkerboard order.  dst has the size and row stride of src.
+void sap_block_major(const Exec &e, const int b[4], int parity, int rows, const void *src, void *dst);
 
 // ---- fermion force (force.cu) ----------------------------------------------
 // X, Y: internal df64 full fields (even, odd).  Gam: device scratch of

@@ -11,7 +11,9 @@
 // dot products are CTA-local reductions, so an MR step needs no grid-wide
 // synchronisation.  The block's MR residual and iterate and the odd
 // intermediate live in shared memory, where the hops read their neighbours;
-// links and clover blocks come from the global FP32 copies.
+// links and clover blocks come from block-major FP32 copies (below), so that
+// the sites of one block are contiguous and the half-steps re-read them from
+// L2 in whole cache lines.
 //
 // The residual r = b - D x each block solve starts from is kept up to date
 // block by block instead of by applying D to the whole lattice before every
@@ -37,9 +39,10 @@ struct SapArgs {
     int b[4];                 // block extents (even, dividing the lattice)
     int bvh;                  // sites of one parity in a block (<= SAP_THREADS)
     const int4 *origin;       // lattice coordinates of the first site of each block of the colour
-    const float4 *U[2];       // FP32 links by parity
-    const float4 *Ce;         // C of the even sites
-    const float4 *Ci;         // C^{-1} of the odd sites
+    const float4 *U[2];       // FP32 links by parity, lattice order (face hops)
+    const float4 *Ub[2];      // the same links in block-major order (block hops)
+    const float4 *Ce;         // C of the even sites, block-major
+    const float4 *Ci;         // C^{-1} of the odd sites, block-major
     const float4 *rin[2];     // the blocks' residual before the face update, by parity (rin[1] null: zero)
     const float4 *eface[2];   // the other colour's last correction by parity (null: none yet)
     float4 *rout_e;           // out: the blocks' even residual after the solve
@@ -67,6 +70,19 @@ __device__ __forceinline__ long long sap_global_cb(const Geom &g, const int G[4]
                   g.Vh, B_SAP_GLOBAL);
 }
 
+// Block-major order of one parity's sites: the blocks in lexicographic order
+// of their block coordinates, and inside a block its sites of that parity in
+// the local checkerboard numbering of sap_local.  It is a permutation of the
+// lattice's checkerboard index (every block holds bvh sites of each parity),
+// so a block-major copy has the same size and row stride as the original.
+__device__ __forceinline__ long long sap_block_base(const SapArgs &a, const int O[4])
+{
+    const int n0 = a.g.L[0] / a.b[0], n1 = a.g.L[1] / a.b[1], n2 = a.g.L[2] / a.b[2];
+    const long long blk =
+        O[0] / a.b[0] + (long long)n0 * (O[1] / a.b[1] + (long long)n1 * (O[2] / a.b[2] + (long long)n2 * (O[3] / a.b[3])));
+    return blk * a.bvh;
+}
+
 __device__ __forceinline__ void ld_sm(const float2 *f, int i, cx<float> v[12])
 {
 #pragma unroll
@@ -83,11 +99,12 @@ __device__ __forceinline__ void st_sm(float2 *f, int i, const cx<float> v[12])
 }
 
 // one direction of the block-local hopping sum at the site with local
-// coordinates l (parity p, global coordinates G): the neighbour is read from
-// the shared-memory field `src` of the other parity when it lies in the block
+// coordinates l (parity p, global coordinates G, block-major index base + i):
+// the neighbour is read from the shared-memory field `src` of the other parity
+// when it lies in the block
 template <int MU>
 __device__ __forceinline__ void sap_hop_dir(const SapArgs &a, const float2 *src, const int l[4], const int G[4],
-                                            int p, long long cb, cx<float> acc[12])
+                                            int p, long long base, int i, cx<float> acc[12])
 {
     const int ext = a.b[MU], L = a.g.L[MU];
     const bool whole = ext == L;   // the block spans the direction: the wrap stays inside
@@ -105,13 +122,11 @@ __device__ __forceinline__ void sap_hop_dir(const SapArgs &a, const float2 *src,
         cx<float> m[9];
         float s = 1.0f;
         if (dir == 0) {
-            load_link(a.U[p], a.g.stride, MU, cb, m);
+            load_link(a.Ub[p], a.g.stride, MU, LQ_IDX(base + i, a.g.Vh, B_SAP_GLOBAL), m);
             if (MU == 3 && G[3] + 1 == L) s = (float)a.g.tbc;
             hop_apply<MU, -1>(acc, psi, m, s);
-        } else {
-            int Gm[4] = {G[0], G[1], G[2], G[3]};
-            Gm[MU] = G[MU] == 0 ? L - 1 : G[MU] - 1;
-            load_link(a.U[1 - p], a.g.stride, MU, sap_global_cb(a.g, Gm), m);
+        } else {   // the link of the neighbour at -mu, which lies in the block
+            load_link(a.Ub[1 - p], a.g.stride, MU, LQ_IDX(base + nbi, a.g.Vh, B_SAP_GLOBAL), m);
             if (MU == 3 && G[3] == 0) s = (float)a.g.tbc;
             hop_apply<MU, +1>(acc, psi, m, s);
         }
@@ -120,14 +135,14 @@ __device__ __forceinline__ void sap_hop_dir(const SapArgs &a, const float2 *src,
 
 // acc = sum over the in-block neighbours of (1 -+ g_mu) W psi
 __device__ __forceinline__ void sap_hop(const SapArgs &a, const float2 *src, const int l[4], const int G[4], int p,
-                                        long long cb, cx<float> acc[12])
+                                        long long base, int i, cx<float> acc[12])
 {
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {0.0f, 0.0f};
-    sap_hop_dir<0>(a, src, l, G, p, cb, acc);
-    sap_hop_dir<1>(a, src, l, G, p, cb, acc);
-    sap_hop_dir<2>(a, src, l, G, p, cb, acc);
-    sap_hop_dir<3>(a, src, l, G, p, cb, acc);
+    sap_hop_dir<0>(a, src, l, G, p, base, i, acc);
+    sap_hop_dir<1>(a, src, l, G, p, base, i, acc);
+    sap_hop_dir<2>(a, src, l, G, p, base, i, acc);
+    sap_hop_dir<3>(a, src, l, G, p, base, i, acc);
 }
 
 // The hops across the two faces of the block normal to MU: for every site on
@@ -206,10 +221,10 @@ __device__ __forceinline__ void sap_sum3(float v[3], float *sh)
 }
 
 #ifndef LQ_SAP_MINB
-#define LQ_SAP_MINB 3
+#define LQ_SAP_MINB 4
 #endif
 
-// The CTA asks for three resident blocks per SM (at most 168 registers); the
+// The CTA asks for four resident blocks per SM (at most 128 registers, no spills); the
 // MR iterate and residual live in shared memory, not in registers.  The solve
 // is one loop over half-steps, each one hop into one parity followed by its
 // epilogue, so that a single copy of the hop code serves all of them (the
@@ -236,6 +251,8 @@ __global__ void __launch_bounds__(SAP_THREADS, LQ_SAP_MINB) sap_block_kernel(Sap
         sap_local(a, i, 1, lo);
     }
     const long long st = a.g.stride;
+    const long long base = sap_block_base(a, O);
+    const long long sb = on ? LQ_IDX(base + i, a.g.Vh, B_SAP_GLOBAL) : 0;   // block-major index of the thread's sites
     const int last = 2 * a.m + 2;
     const bool face = a.eface[0] != nullptr;
     if (face) {
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(SAP_THREADS, LQ_SAP_MINB) sap_block_kernel(Sap
         }
         const long long cb = on ? sap_global_cb(a.g, G) : 0;
         cx<float> w[12];
-        if (on && ph > 0) sap_hop(a, p ? (ph == last ? smX : smE) : smO, l, G, p, cb, w);
+        if (on && ph > 0) sap_hop(a, p ? (ph == last ? smX : smE) : smO, l, G, p, base, i, w);
         float d[3] = {0.0f, 0.0f, 0.0f};
         cx<float> pv[12];
         if (on) {
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(SAP_THREADS, LQ_SAP_MINB) sap_block_kernel(Sap
 #pragma unroll
                     for (int k = 0; k < 12; k++) v[k] = -0.5f * w[k];
                 }
-                clover_apply<float>(a.Ci, st, cb, v, pv);
+                clover_apply<float>(a.Ci, st, sb, v, pv);
                 if (ph < last) {
                     st_sm(smO, i, pv);
                 } else {   // x += e on both parities of the site pair; store e and the residual
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(SAP_THREADS, LQ_SAP_MINB) sap_block_kernel(Sap
                 st_sm(smX, i, v);
             } else if (ph > 1) {   // p = C res + 1/2 H_eo t and the dot products
                 ld_sm(smE, i, v);
-                clover_apply<float>(a.Ce, st, cb, v, pv);
+                clover_apply<float>(a.Ce, st, sb, v, pv);
 #pragma unroll
                 for (int k = 0; k < 12; k++) {
                     pv[k] = pv[k] + 0.5f * w[k];
@@ -367,6 +384,7 @@ void sap_blocks(const Exec &e, const SapLaunch &s)
     a.origin = s.origin;
     for (int q = 0; q < 2; q++) {
         a.U[q] = (const float4 *)s.U[q];
+        a.Ub[q] = (const float4 *)s.Ub[q];
         a.rin[q] = (const float4 *)s.rin[q];
         a.eface[q] = (const float4 *)s.eface[q];
         a.eout[q] = (float4 *)s.eout[q];
@@ -386,6 +404,44 @@ void sap_blocks(const Exec &e, const SapLaunch &s)
     Launch L_(e, K_SAP, sites * (2 * 96 + 2 * 192 + 3 * 96 + 8 * 48 + 2 * 288 + (face ? 2 * 96 : 0)),
               sites * ((2 * s.m + 2 + (face ? 0.5 : 0.0)) * (1320 + 552) + s.m * 100));
     sap_block_kernel<<<s.count, SAP_THREADS, 0, e.st>>>(a);
+}
+
+// dst[r][d] = src[r][s(d)] for the `rows` float4 rows of a parity-p FP32 field
+// (row stride g.stride), d running over the block-major order of the blocks
+// with extents b and s(d) the lattice checkerboard index of the same site.
+// Writes are coalesced; a read touches the b0/2 consecutive sites of one
+// block row.
+__global__ void __launch_bounds__(256) sap_block_major_kernel(Geom g, int4 b, int bvh, int parity, int rows,
+                                                              const float4 *__restrict__ src, float4 *__restrict__ dst)
+{
+    const long long d = blockIdx.x * 256LL + threadIdx.x;
+    if (d >= g.Vh) return;
+    const long long blk = d / bvh;
+    const int i = (int)(d - blk * bvh);
+    const int n0 = g.L[0] / b.x, n1 = g.L[1] / b.y, n2 = g.L[2] / b.z;
+    const int B[4] = {(int)(blk % n0), (int)((blk / n0) % n1), (int)((blk / ((long long)n0 * n1)) % n2),
+                      (int)(blk / ((long long)n0 * n1 * n2))};
+    const int bx2 = b.x >> 1;
+    const int row = i / bx2;
+    int l[4];
+    l[1] = row % b.y;
+    l[2] = (row / b.y) % b.z;
+    l[3] = row / (b.y * b.z);
+    l[0] = 2 * (i - row * bx2) + ((l[1] + l[2] + l[3] + parity) & 1);
+    const int G[4] = {B[0] * b.x + l[0], B[1] * b.y + l[1], B[2] * b.z + l[2], B[3] * b.w + l[3]};
+    const long long s = LQ_IDX((G[0] + (long long)g.L[0] * (G[1] + (long long)g.L[1] * (G[2] + (long long)g.L[2] * G[3]))) >> 1,
+                               g.Vh, B_SAP_GLOBAL);
+    for (int r = 0; r < rows; r++) dst[r * g.stride + d] = src[r * g.stride + s];
+}
+
+void sap_block_major(const Exec &e, const int b[4], int parity, int rows, const void *src, void *dst)
+{
+    const Geom &g = e.g;
+    if (g.Vh == 0) return;
+    Launch L_(e, K_LAYOUT, (double)g.Vh * rows * 32);
+    const int bvh = b[0] * b[1] * b[2] * b[3] / 2;
+    sap_block_major_kernel<<<(unsigned)((g.Vh + 255) / 256), 256, 0, e.st>>>(
+        g, make_int4(b[0], b[1], b[2], b[3]), bvh, parity, rows, (const float4 *)src, (float4 *)dst);
 }
 
 }  // namespace lq
