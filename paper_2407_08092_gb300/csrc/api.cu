@@ -319,6 +319,30 @@ void op_reconstruct(lq_ctx *c, int prec, const void *bo, const void *xe, void *x
     hop(e, r);
 }
 
+// The reconstruction of Eq. 2 together with the full system's residual r = b - D x
+// (prec FP64 or df64): x_o = D_oo^{-1} u with u = b_o - D_oe x_e, and in the same
+// launch r_o = u - D_oo x_o; then r_e = b_e - D_ee x_e - D_eo x_o in one launch.
+void op_reconstruct_residual(lq_ctx *c, int prec, const void *be, const void *bo, const void *xe, void *xo,
+                             void *re, void *ro)
+{
+    Exec e = c->ex();
+    HopCall r = hopcall(c, HOP_RECON_RES, prec, 1);
+    r.in = xe;
+    r.in2 = bo;
+    r.out = xo;
+    r.clov = Cip(c, prec);
+    r.clov2 = Cp(c, prec, 1);
+    r.out2 = ro;
+    hop(e, r);
+    HopCall q = hopcall(c, HOP_RES, prec, 0);
+    q.in = xo;
+    q.in2 = xe;
+    q.b = be;
+    q.out = re;
+    q.clov = Cp(c, prec, 0);
+    hop(e, q);
+}
+
 // ---- Krylov solvers ---------------------------------------------------------------
 
 struct KResult {
@@ -1673,11 +1697,8 @@ lq_status lq_solve(lq_ctx *c, const lq_solver_params *p, const void *b, void *x,
             R.relres = r.relres;
             est_conv = r.converged;
             cycles_left -= r.cycles;
-            op_reconstruct(c, W, bo, xe, xo);
-            // true residual on the full lattice, in W
-            op_full(c, W, xe, xo, ye, yo);
-            axpby(e, W, 1.0, 0.0, be, -1.0, 0.0, ye);
-            axpby(e, W, 1.0, 0.0, bo, -1.0, 0.0, yo);
+            // x_o and the true residual on the full lattice, in W
+            op_reconstruct_residual(c, W, be, bo, xe, xo, ye, yo);
             norm2(e, W, ye, c->red, 0);
             norm2(e, W, yo, c->red, 1);
             reduce_finish(e, c->red, 0, 2);
@@ -1956,11 +1977,9 @@ lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rh
             void *ye = field(ml, PDF, "bw:ye"), *yo = field(ml, PDF, "bw:yo");
             for (int r = 0; r < n_rhs[l]; r++) {
                 const int k = G->first[l] + r;
-                op_reconstruct(ml, PDF, q.BO + r * q.fw, q.XE + r * q.fw, q.XO + r * q.fw);
+                op_reconstruct_residual(ml, PDF, q.BE + r * q.fw, q.BO + r * q.fw, q.XE + r * q.fw,
+                                        q.XO + r * q.fw, ye, yo);
                 export_full(e, PDF, q.XE + r * q.fw, q.XO + r * q.fw, (char *)x[l] + r * q.nat);
-                op_full(ml, PDF, q.XE + r * q.fw, q.XO + r * q.fw, ye, yo);
-                axpby(e, PDF, 1.0, 0.0, q.BE + r * q.fw, -1.0, 0.0, ye);
-                axpby(e, PDF, 1.0, 0.0, q.BO + r * q.fw, -1.0, 0.0, yo);
                 norm2(e, PDF, ye, ml->red, 0);
                 norm2(e, PDF, yo, ml->red, 1);
                 norm2(e, PDF, q.BE + r * q.fw, ml->red, 2);

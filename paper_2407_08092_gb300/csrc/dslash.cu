@@ -54,6 +54,8 @@ struct HopArgs {
     const V *Uout;   // links of the output parity: forward links U_mu(x)
     const V *Uin;    // links of the input parity: backward links U_mu(x - mu)
     const V *clov;
+    const V *clov2;  // HOP_RECON_RES: C of the output parity
+    V *out2;         // HOP_RECON_RES: the residual
     R omega;
     int pout;
     int nrhs;        // right-hand sides sharing the links and clover of this launch
@@ -66,7 +68,7 @@ struct HopArgs {
 template <typename R, int MODE, typename SV, typename LV, typename CV>
 __device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV *Uin, const CV *clov, R omega,
                                          const SV *in, const SV *in2, const SV *bv, SV *out, long long s,
-                                         const Coords &c)
+                                         const Coords &c, const CV *clov2 = nullptr, SV *out2 = nullptr)
 {
     const long long st = g.stride;
     cx<R> acc[12];
@@ -113,11 +115,11 @@ __device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV
 #pragma unroll
         for (int i = 0; i < 12; i++) acc[i] = R(-0.5) * acc[i];
         clover_apply<R>(clov, st, s, acc, v);
-    } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {
+    } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL || MODE == HOP_RES) {
         cx<R> x[12];
         load_spinor_rw(in2, st, s, x);
         clover_apply<R>(clov, st, s, x, v);
-        const R f = MODE == HOP_FULL ? R(-0.5) : R(0.5);
+        const R f = (MODE == HOP_FULL || MODE == HOP_RES) ? R(-0.5) : R(0.5);
 #pragma unroll
         for (int i = 0; i < 12; i++) v[i] = v[i] + f * acc[i];
         if (MODE == HOP_RICH) {
@@ -126,13 +128,26 @@ __device__ __forceinline__ void hop_body(const Geom &g, const LV *Uout, const LV
 #pragma unroll
             for (int i = 0; i < 12; i++) v[i] = x[i] + omega * (bb[i] - v[i]);
         }
-    } else {   // HOP_PREP, HOP_RECON
+        if (MODE == HOP_RES) {
+            cx<R> bb[12];
+            load_spinor(bv, st, s, bb);
+#pragma unroll
+            for (int i = 0; i < 12; i++) v[i] = bb[i] - v[i];
+        }
+    } else {   // HOP_PREP, HOP_RECON, HOP_RECON_RES
         cx<R> y[12];
         load_spinor_rw(in2, st, s, y);
 #pragma unroll
         for (int i = 0; i < 12; i++) y[i] = y[i] + R(0.5) * acc[i];
-        if (MODE == HOP_RECON) {
+        if (MODE == HOP_RECON || MODE == HOP_RECON_RES) {
             clover_apply<R>(clov, st, s, y, v);
+            if (MODE == HOP_RECON_RES) {   // the parity's residual u - C x_o of the x_o just formed
+                cx<R> w[12];
+                clover_apply<R>(clov2, st, s, v, w);
+#pragma unroll
+                for (int i = 0; i < 12; i++) w[i] = y[i] - w[i];
+                store_spinor(out2, st, s, w);
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < 12; i++) v[i] = y[i];
@@ -240,7 +255,7 @@ __global__ void LQ_HOP_BOUNDS hop_kernel(Geom g, HopArgs<R> k)
         hop_body<R, MODE>(g, (const F4S *)k.Uout, (const F4S *)k.Uin, (const F4S *)k.clov, k.omega, k.in, k.in2,
                           k.b, k.out, s, c);
     else
-        hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c);
+        hop_body<R, MODE>(g, k.Uout, k.Uin, k.clov, k.omega, k.in, k.in2, k.b, k.out, s, c, k.clov2, k.out2);
 }
 
 // The same for FP32 K2 and its Richardson form, asked to fit six blocks per SM
@@ -534,7 +549,7 @@ __device__ __forceinline__ cx<df64> rot_i(cx<df64> z, int q)   // i^q z
 
 template <int MODE>
 __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &k, const df2 *in, const df2 *in2,
-                                            const df2 *bv, df2 *out, long long s, const Coords &c)
+                                            const df2 *bv, df2 *out, df2 *out2, long long s, const Coords &c)
 {
     // per direction d = 2 mu + (backward): the partner of h0 is psi_3 for x, y
     // and psi_2 for z, t (acc_2 takes u_1 resp. u_0); the i-powers
@@ -635,8 +650,8 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
             herm6_fma_df(Cb, st, a6, y);
 #pragma unroll
             for (int i = 0; i < 6; i++) y[i] = dl_cnorm(y[i]);
-        } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL) {   // y = C x +- 1/2 acc
-            const float f = MODE == HOP_FULL ? -0.5f : 0.5f;
+        } else if (MODE == HOP_K2 || MODE == HOP_RICH || MODE == HOP_FULL || MODE == HOP_RES) {   // y = C x +- 1/2 acc
+            const float f = (MODE == HOP_FULL || MODE == HOP_RES) ? -0.5f : 0.5f;
             cx<df64> x6[6];
 #pragma unroll
             for (int i = 0; i < 6; i++) {
@@ -650,6 +665,10 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
 #pragma unroll
                 for (int i = 0; i < 6; i++) y[i] = x6[i] + k.omega * (df2_cx(ldg(bv + o + i * st)) - y[i]);
             }
+            if (MODE == HOP_RES) {   // b - D x
+#pragma unroll
+                for (int i = 0; i < 6; i++) y[i] = df2_cx(ldg(bv + o + i * st)) - y[i];
+            }
         } else {   // y = in2 + 1/2 acc, and for the reconstruction C^{-1} of that
 #pragma unroll
             for (int i = 0; i < 6; i++) {
@@ -657,12 +676,20 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
                 dl_cadd(t, {dl_scale2(a6[i].re, 0.5f), dl_scale2(a6[i].im, 0.5f)});
                 a6[i] = dl_cnorm(t);
             }
-            if (MODE == HOP_RECON) {
+            if (MODE == HOP_RECON || MODE == HOP_RECON_RES) {
 #pragma unroll
                 for (int i = 0; i < 6; i++) y[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
                 herm6_fma_df(Cb, st, a6, y);
 #pragma unroll
                 for (int i = 0; i < 6; i++) y[i] = dl_cnorm(y[i]);
+                if (MODE == HOP_RECON_RES) {   // the parity's residual u - C x_o of the x_o just formed
+                    cx<df64> z[6];
+#pragma unroll
+                    for (int i = 0; i < 6; i++) z[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+                    herm6_fma_df(k.clov2 + (long long)blk * 18 * st + s, st, y, z);
+#pragma unroll
+                    for (int i = 0; i < 6; i++) out2[o + i * st] = cx_df2(a6[i] - dl_cnorm(z[i]));
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < 6; i++) y[i] = a6[i];
@@ -677,7 +704,7 @@ __device__ __forceinline__ void hop_df_body(const Geom &g, const HopArgs<df64> &
 #define LQ_DF_MINB 1
 #endif
 template <int MODE>
-__global__ void __launch_bounds__(128, LQ_DF_MINB) hop_df_kernel(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(128, MODE == HOP_RECON_RES ? 3 : LQ_DF_MINB) hop_df_kernel(const __grid_constant__ Geom g,
                                                      const __grid_constant__ HopArgs<df64> k)
 {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -686,7 +713,8 @@ __global__ void __launch_bounds__(128, LQ_DF_MINB) hop_df_kernel(const __grid_co
 #pragma unroll 1
     for (int r = 0; r < k.nrhs; r++) {
         const long long o = r * k.fs;
-        hop_df_body<MODE>(g, k, k.in + o, k.in2 ? k.in2 + o : nullptr, k.b ? k.b + o : nullptr, k.out + o, s, c);
+        hop_df_body<MODE>(g, k, k.in + o, k.in2 ? k.in2 + o : nullptr, k.b ? k.b + o : nullptr, k.out + o,
+                          k.out2 ? k.out2 + o : nullptr, s, c);
     }
 }
 
@@ -714,6 +742,8 @@ static void launch_hop(const Exec &e, const HopCall &c)
     k.Uout = (const V *)c.U[c.pout];
     k.Uin = (const V *)c.U[1 - c.pout];
     k.clov = (const V *)c.clov;
+    k.clov2 = (const V *)c.clov2;
+    k.out2 = (V *)c.out2;
     k.omega = R(c.omega);
     k.pout = c.pout;
     k.nrhs = c.nrhs;
@@ -732,6 +762,7 @@ static void launch_hop(const Exec &e, const HopCall &c)
             kr.in2 = k.in2 ? k.in2 + o : nullptr;
             kr.b = k.b ? k.b + o : nullptr;
             kr.out = k.out + o;
+            kr.out2 = k.out2 ? k.out2 + o : nullptr;
             if constexpr (std::is_same<R, float>::value && (MODE == HOP_K2 || MODE == HOP_RICH))
                 hop_kernel_occ<R, MODE><<<blocks, LQ_HOP_THREADS, 0, e.st>>>(e.g, kr);
             else
@@ -755,6 +786,8 @@ static double hop_site_bytes(int mode, int prec, int nrhs)
     case HOP_RICH: once += cl; per += 2 * sp; break;
     case HOP_PREP: per += sp; break;
     case HOP_RECON: once += cl; per += sp; break;
+    case HOP_RES: once += cl; per += 2 * sp; break;                  // x, b
+    case HOP_RECON_RES: once += 2 * cl; per += 2 * sp; break;        // C^{-1} and C; b in, x and r out
     }
     return once + nrhs * per;
 }
@@ -770,8 +803,9 @@ static int hop_class(int mode, int prec)
 // algorithmic flops per site: 1320 for the eight hops (projection 12, two
 // SU(3) mat-vecs 132, accumulation 24, per direction, less the first
 // accumulation), 552 per clover-block pair, 24 per spinor add / scale
-static const double c_hop_flops[6] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
-                                      1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552};
+static const double c_hop_flops[8] = {1320 + 552, 1320 + 552 + 24, 1320 + 552 + 24 + 48,
+                                      1320 + 552 + 24, 1320 + 24, 1320 + 24 + 552,
+                                      1320 + 552 + 48, 1320 + 24 + 2 * 552 + 24};
 
 double hop_bytes(int mode, int prec, int nrhs, double sites) { return sites * hop_site_bytes(mode, prec, nrhs); }
 double hop_flops(int mode, double site_rhs) { return site_rhs * c_hop_flops[mode]; }
@@ -846,6 +880,14 @@ void hop(const Exec &e, const HopCall &c)
         LQ_CASE(HOP_FULL)
         LQ_CASE(HOP_PREP)
         LQ_CASE(HOP_RECON)
+    case HOP_RES:   // FP64 and df64 only (the solve's full residual)
+        if (c.prec == P64) launch_hop<double, HOP_RES>(e, c);
+        else if (c.prec == PDF) launch_hop<df64, HOP_RES>(e, c);
+        break;
+    case HOP_RECON_RES:
+        if (c.prec == P64) launch_hop<double, HOP_RECON_RES>(e, c);
+        else if (c.prec == PDF) launch_hop<df64, HOP_RECON_RES>(e, c);
+        break;
     }
 #undef LQ_CASE
 }

@@ -166,7 +166,11 @@ enum HopMode {
     HOP_RICH = 2,   // out = in2 + w (b - (C in2 + 1/2 acc))   Richardson sweep on D_S
     HOP_FULL = 3,   // out = C in2 - 1/2 acc               D on one parity
     HOP_PREP = 4,   // out = in2 + 1/2 acc                 b_e - D_eo t_o
-    HOP_RECON = 5   // out = Cinv (in2 + 1/2 acc)          D_oo^{-1} (b_o - D_oe x_e)
+    HOP_RECON = 5,  // out = Cinv (in2 + 1/2 acc)          D_oo^{-1} (b_o - D_oe x_e)
+    // the full system's residual after a solve (FP64 and df64 only):
+    HOP_RES = 6,        // out = b - (C in2 - 1/2 acc)               r_e = b_e - D_ee x_e - D_eo x_o
+    HOP_RECON_RES = 7   // u = in2 + 1/2 acc: out = Cinv u,          x_o = D_oo^{-1} (b_o - D_oe x_e)
+                        //                    out2 = u - clov2 out   r_o = b_o - D_oe x_e - D_oo x_o
 };
 struct HopCall {
     int mode;
@@ -178,6 +182,8 @@ struct HopCall {
     void *out;
     const void *U[2];      // link copies of both parities (this precision)
     const void *clov;      // C or C^{-1} of the output parity (this precision)
+    const void *clov2 = nullptr;   // HOP_RECON_RES: C of the output parity
+    void *out2 = nullptr;          // HOP_RECON_RES: the output parity's residual
     double omega;          // HOP_RICH weight
     int nrhs = 1;          // right-hand sides: in, in2, b, out are nrhs consecutive fields
 };
