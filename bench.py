@@ -266,6 +266,11 @@ def traffic_per_launch(cls_name: str, V: int):
 # 5.37 TFLOP/s FP64-equivalent.
 ALU_F64 = {"hop_k1_f64", "hop_k2_f64"}
 ALU_DF64 = {"hop_k1_df64", "hop_k2_df64", "hop_other", "clover", "clover_field", "force"}
+# FP32 kernels whose data sit in L2 for most of their work (the SAP block solves
+# re-read each block's links and clover on every half-step): their DRAM traffic
+# is near their algorithmic bytes but far below the bandwidth, so they are
+# reported against the same issue ceiling, with the HBM fraction beside it.
+ISSUE_F32 = {"sap"}
 SM_MHZ_MAX = 2070.0
 ISSUE_PEAK_G = 152 * 4 * SM_MHZ_MAX / 1e3   # G warp instructions per second
 
@@ -295,17 +300,18 @@ def roofline_of(name, d, pk, V):
             "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
             "algorithmic_flops_per_launch": d["flops"] / d["launches"],
             "gbs": round(d["bytes"] / t / 1e9, 1), "hbm_frac": round(d["bytes"] / t / 1e9 / pk["hbm_gbs"], 4)}
-    inst = table_per_launch("issue.txt", name, V) if name in ALU_DF64 else None
+    inst = table_per_launch("issue.txt", name, V) if name in ALU_DF64 or name in ISSUE_F32 else None
     if inst is not None:
         # instructions per launch over the launch's average duration, against the issue ceiling
         ach = inst / (d["ms"] / d["launches"] / 1e3) / 1e9
-        model = d["flops"] / t / 1e12 / (152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2 / 1e12)
         base.update({"bound": "issue", "achieved": round(ach, 1), "peak": round(ISSUE_PEAK_G, 1),
                      "unit": "Gwarp-inst/s", "frac": round(ach / ISSUE_PEAK_G, 4),
                      "traffic": traffic_per_launch(name, V),
                      "peak_src": f"hardware issue ceiling: 152 SMs x 4 schedulers x {SM_MHZ_MAX:.0f} MHz; "
-                                 "instructions from ncu sm__inst_executed.sum (profiles/issue.txt)",
-                     "df64_model_frac": round(model, 4)})
+                                 "instructions from ncu sm__inst_executed.sum (profiles/issue.txt)"})
+        if name in ALU_DF64:
+            model = d["flops"] / t / 1e12 / (152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2 / 1e12)
+            base["df64_model_frac"] = round(model, 4)
     elif name in ALU_F64 or name in ALU_DF64:
         peak = (152 * 2 * 2 * SM_MHZ_MAX * 1e6 if name in ALU_F64 else 152 * 128 * SM_MHZ_MAX * 1e6 / 15 * 2) / 1e12
         ach = d["flops"] / t / 1e12
@@ -936,7 +942,8 @@ def run_ours(args):
             "frac": (force.get("roofline") or {}).get("frac")},
         "sap": None if sap is None else {
             "sap34_ms": sap["sap_3_4_ms"], "rich5_ms": sap["richardson_5_ms"], "fgmres_sap_ms": sap["fgmres_sap_ms"],
-            "frac": (sap.get("roofline") or {}).get("frac")},
+            "bound": (sap.get("roofline") or {}).get("bound"), "frac": (sap.get("roofline") or {}).get("frac"),
+            "hbm_frac": (sap.get("roofline") or {}).get("hbm_frac")},
         "bf16": None if bf16 is None else pick(bf16["bf16"], "ds_us", "ds_frac", "rel_err_vs_fp64"),
         # df64 classes against the SMs' instruction-issue ceiling (ncu-counted
         # instructions per launch over the live launch time); the 15-instruction
