@@ -19,7 +19,7 @@ __device__ __forceinline__ void to_f(const cx<double> a[12], cx<float> v[12])
 __device__ __forceinline__ void to_f(const cx<df64> a[12], cx<float> v[12])
 {
 #pragma unroll
-    for (int k = 0; k < 12; k++) v[k] = {(float)df_to_double(a[k].re), (float)df_to_double(a[k].im)};
+    for (int k = 0; k < 12; k++) v[k] = {df_to_float(a[k].re), df_to_float(a[k].im)};
 }
 
 // any internal precision -> BF16

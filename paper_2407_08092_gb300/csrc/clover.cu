@@ -36,8 +36,8 @@ __device__ __forceinline__ void store_block_df32(const Geom &g, int b, long long
         const df64 a0 = r[4 * k], a1 = r[4 * k + 1], a2 = r[4 * k + 2], a3 = r[4 * k + 3];
         Cdf[(b * 18 + 2 * k) * g.stride + s] = df2{a0.hi, a0.lo, a1.hi, a1.lo};
         Cdf[(b * 18 + 2 * k + 1) * g.stride + s] = df2{a2.hi, a2.lo, a3.hi, a3.lo};
-        C32[(b * 9 + k) * g.stride + s] = make_float4((float)df_to_double(a0), (float)df_to_double(a1),
-                                                      (float)df_to_double(a2), (float)df_to_double(a3));
+        C32[(b * 9 + k) * g.stride + s] =
+            make_float4(df_to_float(a0), df_to_float(a1), df_to_float(a2), df_to_float(a3));
     }
 }
 __device__ __forceinline__ void store_pair(df2 *p, df64 a, df64 b) { *p = df2{a.hi, a.lo, b.hi, b.lo}; }

@@ -168,12 +168,17 @@ __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b;
 // remainder m - hi, an integer R with |R| <= 2^28 in units of 2^(e-52), gives
 // lo = RN(R) 2^(e-52) -- the same values as hi = (float)d, lo = (float)(d - hi).
 // Zero, subnormal, very small or very large magnitudes and non-finite values
-// take the FP64 route.
+// take the FP64 route, kept out of line: inlined, the compiler evaluates it for
+// every value and selects (four FP64-pipe operations per double, which then
+// bound the link import).
+static __device__ __noinline__ df64 df_split_rare(double d) { return df64(d); }
+static __device__ __noinline__ double f2d_rare(float x) { return (double)x; }
+
 __device__ __forceinline__ df64 df_split(double d)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if (e < -74 || e > 126) return df64(d);
+    if (e < -74 || e > 126) return df_split_rare(d);
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     unsigned q = (unsigned)(m >> 29);             // 2^23 <= q < 2^24
     int R = (int)(m & 0x1FFFFFFFull);             // 0 <= R < 2^29
@@ -199,7 +204,7 @@ __device__ __forceinline__ double f2d_bits(float x)
     const unsigned b = __float_as_uint(x);
     const unsigned E = (b >> 23) & 0xFFu;
     if (E == 0u && (b & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
-    if (E == 0u || E == 0xFFu) return (double)x;
+    if (E == 0u || E == 0xFFu) return f2d_rare(x);
     return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
                                             ((unsigned long long)(E + 896u) << 52) |
                                             ((unsigned long long)(b & 0x7FFFFFu) << 29)));
@@ -209,6 +214,8 @@ __device__ __forceinline__ double df_join(float hi, float lo) { return f2d_bits(
 
 __device__ __forceinline__ bool df_positive(df64 a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+// hi + lo rounded to FP32: one float add, which rounds the exact sum once
+__device__ __forceinline__ float df_to_float(df64 a) { return a.hi + a.lo; }
 
 // ---------------------------------------------------------------------------
 // Lazily normalised df64 sums (compensated dot product in the manner of Ogita,
