@@ -319,8 +319,9 @@ typedef enum {
     LQ_K_DOT_F64, LQ_K_DOT_F32,    /* multi-dot products */
     LQ_K_AXPY_F64, LQ_K_AXPY_F32,  /* axpby / multi-axpy */
     LQ_K_NORM,           /* norms */
-    LQ_K_FINISH,         /* second stage of the deterministic reductions */
-    LQ_K_COPY,           /* device memset / memcpy steps (not kernels) */
+    LQ_K_FINISH,         /* second stage of the deterministic reductions, and the small kernels
+                            that move solver scalars between host and device */
+    LQ_K_COPY,           /* field copies (a kernel) and memsets (not kernels) */
     LQ_K_HOP_K1_DF64, LQ_K_HOP_K2_DF64,   /* K1, K2 in df64 */
     LQ_K_DOT_DF64, LQ_K_AXPY_DF64,        /* BLAS-1 in df64 */
     LQ_K_CLOVER_FIELD,   /* field strengths F_munu of the six planes from the leaves (df64) */

@@ -61,6 +61,8 @@ struct lq_ctx {
     int *dflag = nullptr;
     RedScratch red{};
     double *h_pin = nullptr;   // pinned host mirror of red.out / coefficients
+    double *h_pin_dev = nullptr;   // h_pin's device mapping (written by get_values)
+    int *h_int = nullptr, *h_int_dev = nullptr;   // pinned host ints and their device mapping
     double *d_coef = nullptr;  // device coefficients [2 * RED_SLOTS]
     double *d_s2 = nullptr;    // device: squared scales s_j^2 of the FP32 GMRES basis [RED_SLOTS]
     std::map<std::string, std::pair<void *, size_t>> ws;
@@ -166,9 +168,8 @@ void sync(lq_ctx *c) { ck(c, cudaStreamSynchronize(c->st), "cudaStreamSynchroniz
 // copy r.out[first .. first+count) (complex slots) to the pinned mirror and wait
 const double *fetch(lq_ctx *c, int first, int count)
 {
-    ck(c, cudaMemcpyAsync(c->h_pin + 2 * first, c->red.out + 2 * first, sizeof(double) * 2 * count,
-                          cudaMemcpyDeviceToHost, c->st),
-       "cudaMemcpyAsync D2H");
+    get_values(c->ex(), c->red.out + 2 * first, 2 * count, c->h_pin_dev + 2 * first);
+    ck_launch(c, "fetch");
     sync(c);
     return c->h_pin + 2 * first;
 }
@@ -405,15 +406,14 @@ struct Hess {
 
 void upload_coef(lq_ctx *c, const std::vector<cd> &y)
 {
+    std::vector<double> v(2 * y.size());
     for (size_t j = 0; j < y.size(); j++) {
-        c->h_pin[2 * RED_SLOTS + 2 * j] = y[j].real();
-        c->h_pin[2 * RED_SLOTS + 2 * j + 1] = y[j].imag();
+        v[2 * j] = y[j].real();
+        v[2 * j + 1] = y[j].imag();
     }
-    ck(c, cudaMemcpyAsync(c->d_coef, c->h_pin + 2 * RED_SLOTS, sizeof(double) * 2 * y.size(), cudaMemcpyHostToDevice,
-                          c->st),
-       "cudaMemcpyAsync H2D");
-    // the pinned staging area is reused by the next upload: wait for this copy
-    sync(c);
+    // kernel arguments: nothing to stage, so nothing to wait for
+    put_values(c->ex(), v.data(), (int)v.size(), c->d_coef);
+    ck_launch(c, "upload_coef");
 }
 
 // Arnoldi step: w <- w orthogonalised against V[0..k] by CGS2; returns the
@@ -455,14 +455,12 @@ double arnoldi_cgs2(lq_ctx *c, int prec, void *V, int k, void *w, Hess &H)
 
 // The FP32 GMRES keeps its basis unnormalised: v_j = s_j V_j with the scales
 // s_j on the host, which saves the pass that would scale each new vector by
-// 1 / ||w||.  set_scale stages s_j^2 for the device-side CGS coefficients
-// (each slot is written once per cycle; the stream has synchronised since its
-// previous copy, at every Arnoldi step's fetch).
+// 1 / ||w||.  set_scale passes s_j^2 to the device for the CGS coefficients.
 void set_scale(lq_ctx *c, int j, double s)
 {
-    c->h_pin[4 * RED_SLOTS + j] = s * s;
-    ck(c, cudaMemcpyAsync(c->d_s2 + j, c->h_pin + 4 * RED_SLOTS + j, sizeof(double), cudaMemcpyHostToDevice, c->st),
-       "cudaMemcpyAsync H2D");
+    const double s2 = s * s;
+    put_values(c->ex(), &s2, 1, c->d_s2 + j);
+    ck_launch(c, "set_scale");
 }
 
 // Arnoldi step on the unnormalised FP32 basis: w = D_S V_k = D_S v_k / s_k.
@@ -890,6 +888,8 @@ struct lq_group {
     std::vector<double> cap_bytes;
     double *h = nullptr;           // pinned: est / norms [N], targets [N], norms [N]
     int *hact = nullptr;           // pinned: active flags [N]
+    double *h_dev = nullptr;       // device mappings of h and hact (written by get_values / get_ints)
+    int *hact_dev = nullptr;
     std::vector<void *> owned;
 };
 
@@ -1065,6 +1065,8 @@ void group_setup(lq_group *G, const std::vector<int> &nrhs, int m)
     }
     ck(c, cudaMallocHost((void **)&G->h, sizeof(double) * 3 * N), "cudaMallocHost");
     ck(c, cudaMallocHost((void **)&G->hact, sizeof(int) * N), "cudaMallocHost");
+    ck(c, cudaHostGetDevicePointer((void **)&G->h_dev, G->h, 0), "cudaHostGetDevicePointer");
+    ck(c, cudaHostGetDevicePointer((void **)&G->hact_dev, G->hact, 0), "cudaHostGetDevicePointer");
     G->nrhs = nrhs;
     group_tiles(G, G->pin_spt, G->pin_rpt);
     G->tune.grid = group_grid(G, G->pin_factor);
@@ -1259,8 +1261,8 @@ int group_run_cycle(lq_group *G)
     group_segment(G, 0);
     int steps = 0;
     for (int j = 1; j <= nseg; j++) {
-        ck(c, cudaMemcpyAsync(G->hact, G->ks.active, sizeof(int) * G->N, cudaMemcpyDeviceToHost, G->st),
-           "cudaMemcpyAsync D2H");
+        get_ints(gexec(G), G->ks.active, G->N, G->hact_dev);
+        ck_launch(c, "active flags");
         ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
         bool any = false;
         for (int r = 0; r < G->N; r++) any = any || G->hact[r];
@@ -1415,6 +1417,9 @@ lq_status lq_create(lq_ctx **out, const lq_lattice *lat, void *stream)
         c->dflag = (int *)dev_alloc(c, sizeof(int));
         // pinned: [0, 2R) red.out mirror, [2R, 4R) coefficients, [4R, 5R) basis scales
         ck(c, cudaMallocHost((void **)&c->h_pin, sizeof(double) * 5 * RED_SLOTS), "cudaMallocHost");
+        ck(c, cudaHostGetDevicePointer((void **)&c->h_pin_dev, c->h_pin, 0), "cudaHostGetDevicePointer");
+        ck(c, cudaMallocHost((void **)&c->h_int, sizeof(int) * 4), "cudaMallocHost");
+        ck(c, cudaHostGetDevicePointer((void **)&c->h_int_dev, c->h_int, 0), "cudaHostGetDevicePointer");
     } catch (const Fail &f) {
         lq_destroy(c);
         return f.s;
@@ -1431,6 +1436,7 @@ lq_status lq_destroy(lq_ctx *c)
     for (void *p : c->owned)
         if (p) cudaFree(p);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->h_int) cudaFreeHost(c->h_int);
     for (cudaEvent_t ev : c->prof.pool) cudaEventDestroy(ev);
     delete c;
     return LQ_OK;
@@ -1474,9 +1480,10 @@ lq_status lq_set_gauge(lq_ctx *c, const void *U)
         ck(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "cudaMemsetAsync");
         clover_invert(e, c->Cdf[1], c->Cidf, c->Ci32, c->dflag);
         ck_launch(c, "set_gauge kernels");
-        int flag = 0;
-        ck(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "cudaMemcpyAsync");
+        get_ints(e, c->dflag, 1, c->h_int_dev);
+        ck_launch(c, "set_gauge flag");
         sync(c);
+        const int flag = c->h_int[0];
         if (flag) fail(c, LQ_ERR_BREAKDOWN, std::to_string(flag) + " clover blocks with a non-positive pivot");
         c->have_gauge = true;
     });
@@ -1940,13 +1947,13 @@ lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rh
                 G->h[N + k] = done ? rn[k] * 2.0 : p->smooth_tol * rn[k];   // converged ones stay idle
                 if (!done) outer[k]++;
             }
-            ck(c, cudaMemcpyAsync(G->ks.target, G->h + N, sizeof(double) * N, cudaMemcpyHostToDevice, G->st),
-               "cudaMemcpyAsync H2D");
+            put_values(gexec(G), G->h + N, N, G->ks.target);
+            ck_launch(c, "inner targets");
             ck(c, cudaMemsetAsync(G->ks.nanflag, 0, sizeof(int), G->st), "cudaMemsetAsync");
             for (int cyc = 0; cyc < p->smooth_n; cyc++) {
                 const int steps = group_run_cycle(G);
-                ck(c, cudaMemcpyAsync(G->h, G->ks.est, sizeof(double) * N, cudaMemcpyDeviceToHost, G->st),
-                   "cudaMemcpyAsync D2H");
+                get_values(gexec(G), G->ks.est, N, G->h_dev);
+                ck_launch(c, "inner estimates");
                 ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
                 bool inner_done = true;
                 for (int k = 0; k < N; k++) {
@@ -1955,8 +1962,8 @@ lq_status lq_solve_group(lq_group *G, const lq_solver_params *p, const int *n_rh
                 }
                 if (inner_done) break;
             }
-            ck(c, cudaMemcpyAsync(&G->hact[0], G->ks.nanflag, sizeof(int), cudaMemcpyDeviceToHost, G->st),
-               "cudaMemcpyAsync D2H");
+            get_ints(gexec(G), G->ks.nanflag, 1, G->hact_dev);
+            ck_launch(c, "NaN flag");
             ck(c, cudaStreamSynchronize(G->st), "cudaStreamSynchronize");
             if (G->hact[0]) fail(c, LQ_ERR_NAN, "NaN/Inf in the batched inner solve");
             for (int l = 0; l < M; l++) {

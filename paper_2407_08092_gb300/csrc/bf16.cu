@@ -146,7 +146,7 @@ void bf16_convert(const Exec &e, int from, const void *in, int to, void *out)
         if (from == P64) to_bf16_kernel<double2, double><<<b, 256, 0, e.st>>>(e.g, (const double2 *)in, (BfS4 *)out);
         else if (from == P32) to_bf16_kernel<float4, float><<<b, 256, 0, e.st>>>(e.g, (const float4 *)in, (BfS4 *)out);
         else if (from == PDF) to_bf16_kernel<df2, df64><<<b, 256, 0, e.st>>>(e.g, (const df2 *)in, (BfS4 *)out);
-        else cudaMemcpyAsync(out, in, spinor_bytes(e.g, P16), cudaMemcpyDeviceToDevice, e.st);
+        else copy_bytes(e, in, out, spinor_bytes(e.g, P16));
     } else if (to == P64) {
         bf16_to_d_kernel<<<b, 256, 0, e.st>>>(e.g, (const BfS4 *)in, (double2 *)out);
     } else if (to == P32) {

@@ -396,10 +396,70 @@ void zero(const Exec &e, int prec, void *x)
     cudaMemsetAsync(x, 0, spinor_bytes(e.g, prec), e.st);
 }
 
+__global__ void __launch_bounds__(RT) copy_kernel(const float4 *__restrict__ x, float4 *__restrict__ y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) y[i] = __ldg(x + i);
+}
+
+void copy_bytes(const Exec &e, const void *x, void *y, size_t bytes)
+{
+    const long long n = (long long)(bytes / sizeof(float4));
+    if (n == 0) return;
+    const long long b = (n + RT - 1) / RT;
+    copy_kernel<<<(unsigned)(b < 4 * 608 ? b : 4 * 608), RT, 0, e.st>>>((const float4 *)x, (float4 *)y, n);
+}
+
+// a field copy by a kernel rather than cudaMemcpyAsync, which a copy engine
+// would serve behind any large transfer the caller has queued on another stream
 void copy(const Exec &e, int prec, const void *x, void *y)
 {
-    Launch L_(e, K_COPY, 2.0 * e.g.Vh * sp_bytes(prec));
-    cudaMemcpyAsync(y, x, spinor_bytes(e.g, prec), cudaMemcpyDeviceToDevice, e.st);
+    Launch L_(e, K_COPY, 2.0 * e.g.Vh * sp_bytes(prec), 0.0, true);
+    copy_bytes(e, x, y, spinor_bytes(e.g, prec));
+}
+
+// ---- small host <-> device transfers ------------------------------------------------
+// The solvers exchange a few scalars with the host at every Arnoldi step.  They
+// move through kernels: values to the device as a kernel argument, values to
+// the host written by a kernel into pinned host memory through its device
+// mapping.  A cudaMemcpyAsync would be served by a copy engine in order, behind
+// whatever large transfer the caller has queued on another stream.
+struct SmallVals {
+    double v[kSmallVals];
+};
+__global__ void put_values_kernel(SmallVals s, int n, double *d)
+{
+    if ((int)threadIdx.x < n) d[threadIdx.x] = s.v[threadIdx.x];
+}
+__global__ void get_values_kernel(const double *__restrict__ d, int n, double *h)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = d[i];
+}
+__global__ void get_ints_kernel(const int *__restrict__ d, int n, int *h)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = d[i];
+}
+
+void put_values(const Exec &e, const double *h, int n, double *d)
+{
+    for (int k = 0; k < n; k += kSmallVals) {
+        const int m = n - k < kSmallVals ? n - k : kSmallVals;
+        SmallVals s;
+        for (int i = 0; i < m; i++) s.v[i] = h[k + i];
+        Launch L_(e, K_FINISH, 0.0);
+        put_values_kernel<<<1, kSmallVals, 0, e.st>>>(s, m, d + k);
+    }
+}
+void get_values(const Exec &e, const double *d, int n, double *h_mapped)
+{
+    if (n <= 0) return;
+    Launch L_(e, K_FINISH, 0.0);
+    get_values_kernel<<<1, 128, 0, e.st>>>(d, n, h_mapped);
+}
+void get_ints(const Exec &e, const int *d, int n, int *h_mapped)
+{
+    if (n <= 0) return;
+    Launch L_(e, K_FINISH, 0.0);
+    get_ints_kernel<<<1, 128, 0, e.st>>>(d, n, h_mapped);
 }
 
 void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi, void *y, int nfields)

@@ -225,9 +225,17 @@ __device__ __forceinline__ cx<df64> f_entry(const float2 *__restrict__ Fb, long 
 // Assemble the two packed 6x6 blocks of C(x) from the six field strengths:
 // block b: G1 = -F_yz +- F_xt, G2 = F_xz +- F_yt, G3 = -F_xy +- F_zt (+ for b = 0),
 // M = i h [[G3, G1 - i G2], [G1 + i G2, -G3]], h = c_sw / 2, C = (4 + m0) + M.
-__global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const float2 *__restrict__ Fb, double csw,
-                                                              double m0, df2 *Ce, df2 *Co, float4 *C32e,
-                                                              float4 *C32o)
+// The entries are formed in their packed order and stored four at a time (two
+// df2 and one FP32 float4), so only four of a block's 36 entries are held in
+// registers at once.  diag = 4 + m0 and h come as df64 pairs split on the host.
+// Four resident blocks per SM (128 registers, a few bytes of spills) against
+// two unbounded: 0.60 against 0.74 ms per launch of assembly and inverse on
+// 32^3 x 64, on average.
+#ifndef LQ_CLA_MINB
+#define LQ_CLA_MINB 4
+#endif
+__global__ void __launch_bounds__(128, LQ_CLA_MINB) clover_assemble_kernel(Geom g, const float2 *__restrict__ Fb, df64 diag,
+                                                              df64 h, df2 *Ce, df2 *Co, float4 *C32e, float4 *C32o)
 {
     const long long lex = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (lex >= g.V) return;
@@ -238,7 +246,7 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
     const int parity = (c0 + c1 + c2 + c3) & 1;
     const long long cb = lex >> 1;
     df2 *C = parity ? Co : Ce;
-    const df64 diag(4.0 + m0), h(0.5 * csw);
+    float4 *C32 = parity ? C32o : C32e;
 #pragma unroll 1
     for (int b = 0; b < 2; b++) {
         const bool plus = b == 0;
@@ -250,12 +258,24 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
             const cx<df64> s = l == 1 ? fs : -fs;
             return plus ? s + ft : s - ft;
         };
-        df64 out[36];   // every index below is a constant: the block stays in registers
+        // packed entry k (every k below is a constant): kept until its group of
+        // four is complete, then stored
+        df64 buf[4];
+        auto emit = [&](int k, df64 v) {
+            buf[k & 3] = v;
+            if ((k & 3) == 3) {
+                const int q = k >> 2;
+                C[(b * 18 + 2 * q) * g.stride + cb] = df2{buf[0].hi, buf[0].lo, buf[1].hi, buf[1].lo};
+                C[(b * 18 + 2 * q + 1) * g.stride + cb] = df2{buf[2].hi, buf[2].lo, buf[3].hi, buf[3].lo};
+                C32[(b * 9 + q) * g.stride + cb] =
+                    make_float4(df_to_float(buf[0]), df_to_float(buf[1]), df_to_float(buf[2]), df_to_float(buf[3]));
+            }
+        };
 #pragma unroll
         for (int i = 0; i < 6; i++) {
             const int si = i / 3, ai = i % 3;
             const df64 v = -(h * G(2, ai, ai).im);          // Re(i h G3_aa) = -h Im(G3_aa)
-            out[i] = si == 0 ? diag + v : diag - v;
+            emit(i, si == 0 ? diag + v : diag - v);
         }
 #pragma unroll
         for (int i = 1; i < 6; i++)
@@ -269,11 +289,10 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const floa
                 } else {   // si = 1, sj = 0: i h (G1 + i G2)
                     m = ti(h * (G(0, ai, aj) + ti(G(1, ai, aj))));
                 }
-                const int k = 6 + 2 * tri(i, j);
-                out[k] = m.re;
-                out[k + 1] = m.im;
+                const int k = 6 + 2 * tri(i, j);   // increasing with (i, j) in this order
+                emit(k, m.re);
+                emit(k + 1, m.im);
             }
-        store_block_df32(g, b, cb, out, C, parity ? C32o : C32e);
     }
 }
 
@@ -441,8 +460,11 @@ void clover_build(const Exec &e, const void *Udf[2], double csw, double m0, void
     }
     // reads the six F, writes the blocks in df64 and FP32
     Launch L_(e, K_CLOVER, (double)e.g.V * (6 * 72 + 72 * (8 + 4)));
+    const double dg = 4.0 + m0, hh = 0.5 * csw;
+    const float dg_hi = (float)dg, hh_hi = (float)hh;
     clover_assemble_kernel<<<blocks_for(e.g.V, 128), 128, 0, e.st>>>(
-        e.g, (const float2 *)Fscratch, csw, m0, (df2 *)Cdf[0], (df2 *)Cdf[1], (float4 *)C32[0], (float4 *)C32[1]);
+        e.g, (const float2 *)Fscratch, df64(dg_hi, (float)(dg - (double)dg_hi)), df64(hh_hi, (float)(hh - (double)hh_hi)),
+        (df2 *)Cdf[0], (df2 *)Cdf[1], (float4 *)C32[0], (float4 *)C32[1]);
 }
 
 void clover_invert(const Exec &e, const void *Cdf, void *Cidf, void *Ci32, int *flag)

@@ -49,14 +49,15 @@ struct Exec {
 // Accounts one launch: records a start event at construction and an end
 // event, the launch count, the algorithmic bytes and the algorithmic flops
 // (FP64-equivalent for df64 kernels) at destruction.  Kernel launches count
-// toward `launches`; memset/memcpy steps (K_COPY) do not.
+// toward `launches`; memsets (K_COPY without `kernel_`) do not.
 struct Launch {
     const Exec &e;
     int cls;
     double bytes, flops;
     cudaEvent_t a = nullptr;
-    Launch(const Exec &e_, int cls_, double bytes_, double flops_ = 0.0)
-        : e(e_), cls(cls_), bytes(bytes_), flops(flops_)
+    bool kernel;   // a kernel of the library (counted in `launches`)
+    Launch(const Exec &e_, int cls_, double bytes_, double flops_ = 0.0, bool kernel_ = false)
+        : e(e_), cls(cls_), bytes(bytes_), flops(flops_), kernel(kernel_ || cls_ != K_COPY)
     {
         if (e.prof && e.prof->on) {
             a = e.prof->get();
@@ -65,7 +66,7 @@ struct Launch {
     }
     ~Launch()
     {
-        if (cls != K_COPY) e.ctr->launches++;
+        if (kernel) e.ctr->launches++;
         e.ctr->bytes += bytes;
         if (a) {
             cudaEvent_t b = e.prof->get();
@@ -228,6 +229,16 @@ void clover_mul(const Exec &e, int prec, const void *clov, const void *in, void 
 // spinor_bytes apart).  Complex scalars are (re, im) pairs.
 void zero(const Exec &e, int prec, void *x);
 void copy(const Exec &e, int prec, const void *x, void *y);
+// y = x for `bytes` (a multiple of 16) of device memory, by a kernel
+void copy_bytes(const Exec &e, const void *x, void *y, size_t bytes);
+// Small host <-> device transfers by kernels (see blas.cu): put_values copies
+// n host doubles (passed as kernel arguments, kSmallVals per launch) to device
+// memory; get_values / get_ints copy n device values into pinned host memory
+// given by its device-mapped address.  The host reads them after a stream sync.
+constexpr int kSmallVals = 64;
+void put_values(const Exec &e, const double *h, int n, double *d);
+void get_values(const Exec &e, const double *d, int n, double *h_mapped);
+void get_ints(const Exec &e, const int *d, int n, int *h_mapped);
 // y = a x + b y  (complex a, b; host scalars)
 void axpby(const Exec &e, int prec, double ar, double ai, const void *x, double br, double bi,
            void *y, int nfields = 1);
