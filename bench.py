@@ -786,15 +786,15 @@ def run_ours(args):
     lqdd.lq_profile(ctx, False)
 
     # e2e: host (pinned) inputs and result, copies inside the timed region.  The
-    # inputs are triple-buffered: an upload stream copies step i+2's gauge field
-    # and source while step i computes, and a download stream reads step i's
-    # solution after it.  Two steps of slack absorb the occasional host-device
-    # transfer that takes several times its usual 7.6 ms (measured on these
-    # shared hosts: single uploads of 70-97 ms and downloads of 30-40 ms, a few
-    # times per 20 steps, with or without the clock sampler running).
+    # inputs are buffered four deep: an upload stream copies step i+3's gauge
+    # field and source while step i computes, and a download stream reads step
+    # i's solution after it.  Three steps of slack absorb the occasional
+    # host-device transfer that takes many times its usual 7.6 ms (measured on
+    # these shared hosts: single uploads of 70-139 ms and downloads of 30-43 ms,
+    # a few times per 20 steps, with or without the clock sampler running).
     e2e = None
     if not args.no_e2e:
-        NB = 3
+        NB = 4
         Uh = torch.from_numpy(U).pin_memory()
         bh = torch.from_numpy(b).pin_memory()
         xh = torch.empty_like(bh).pin_memory()
@@ -868,7 +868,7 @@ def run_ours(args):
         e2e_steps.update({k + "_ms": [round(a.elapsed_time(z), 3) for a, z in v] for k, v in tev.items()})
         e2e = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
                "d2h_bytes_per_step": int(xh.numel() * 16), "step_bytes": step_bytes,
-               "overlap": "triple-buffered inputs: step i+2's upload and step i's download on their own streams",
+               "overlap": "inputs buffered four deep: step i+3's upload and step i's download on their own streams",
                "split_median": e2e_split, "per_step": e2e_steps}
         lqdd.lq_set_gauge(ctx, dU)
 
