@@ -256,7 +256,7 @@ def traffic_per_launch(cls_name: str, V: int):
 
 # Kernel classes whose roof is arithmetic, not HBM: native FP64 runs on the
 # FP64 pipe (GB300: 2 FMA/clk/SM -> 152 * 2 * 2 flop * 2.07 GHz = 1.26 TFLOP/s,
-# the nominal 1.25 TFLOP/s), df64 on the FP32 pipe.  A df64 class is judged by
+# the nominal 1.25 TFLOP/s), df64 on the FP32 pipe.  A df64 class is measured by
 # instruction issue: the warp instructions one launch executes (ncu
 # sm__inst_executed.sum per unit site, profiles/issue.txt) over its duration,
 # against the SMs' issue ceiling of 152 SMs x 4 schedulers x 1 warp instruction
