@@ -124,14 +124,23 @@ __global__ void __launch_bounds__(BT, 4) baxpy_kernel(const float4 *__restrict__
     float nrm[1] = {0.0f};
     for (long long i = blockIdx.x * (long long)BT + threadIdx.x; i < len; i += (long long)gridDim.x * BT) {
         float4 yv = yr[i];
-        for (int j = 0; j < nv; j++) {
-            const float4 v = __ldg(Vr + j * vjs + i);
+        auto acc = [&](int j, const float4 v) {
             const float cr = csr[j], ci = csi[j];
             yv.x = fmaf(cr, v.x, fmaf(-ci, v.y, yv.x));
             yv.y = fmaf(cr, v.y, fmaf(ci, v.x, yv.y));
             yv.z = fmaf(cr, v.z, fmaf(-ci, v.w, yv.z));
             yv.w = fmaf(cr, v.w, fmaf(ci, v.z, yv.w));
+        };
+        // four basis loads in flight before their sums (the same order of sums)
+        int j = 0;
+        for (; j + 4 <= nv; j += 4) {
+            float4 vv[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) vv[q] = __ldg(Vr + (j + q) * vjs + i);
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc(j + q, vv[q]);
         }
+        for (; j < nv; j++) acc(j, __ldg(Vr + j * vjs + i));
         yr[i] = yv;
         if (NORM) nrm[0] = fmaf(yv.x, yv.x, fmaf(yv.y, yv.y, fmaf(yv.z, yv.z, fmaf(yv.w, yv.w, nrm[0]))));
     }
