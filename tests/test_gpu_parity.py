@@ -171,6 +171,27 @@ def test_solve(pair, lqdd, kind):
     assert abs(r_true - st.rel_resid_true) <= 1e-3 * r_true + 1e-15
 
 
+def test_long_cycle_solve(lqdd):
+    """GMRES(100) in FP64 (Algorithm 2 with long cycles): the least-squares
+    coefficients of a cycle longer than 32 steps go to the device in more than
+    one kernel-argument chunk of 64 doubles.  The solution is checked with the
+    oracle's D like every other solve."""
+    p = Pair((4, 4, 4, 4), eps=0.25, seed=4321, m0=0.05, csw=1.0)
+    try:
+        b = synth.gaussian_spinor(p.V, 77)
+        x = p.torch.zeros_like(p.dev(b))
+        # the oracle's GMRES(100) needs 39 steps in its first cycle to reach 1e-12
+        # here; the first cycle only ends on that estimate, so iters > 32 means a
+        # cycle of more than 32 steps ran
+        status, st = lqdd.lq_solve(p.ctx, lqdd.make_params(tol=1e-12, restart=100, max_restarts=20), p.dev(b), x)
+        assert status == lqdd.LQ_OK, (lqdd.lq_status_string(status), st.as_dict())
+        assert st.iters > 32, st.as_dict()
+        r_true = _check_solution(p, b, p.host(x), 1e-12)
+        assert abs(r_true - st.rel_resid_true) <= 1e-3 * r_true + 1e-15
+    finally:
+        p.close()
+
+
 def test_solve_matches_oracle_solution(lqdd):
     """On 4^4 the solution itself agrees with the oracle's odd-even GMRES
     solution within the tolerance times a modest condition factor."""
