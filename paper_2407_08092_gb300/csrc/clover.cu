@@ -161,7 +161,10 @@ __device__ __forceinline__ void ah_conj(const M3<df64> &H, const M3<df64> &W, df
 }
 
 // pass 1: H(y) = AH(P(y)), one thread per (site, plane)
-__global__ void __launch_bounds__(128) clover_plaq_kernel(Geom g, const df2 *__restrict__ Ue,
+#ifndef LQ_PLAQ_MINB
+#define LQ_PLAQ_MINB 4
+#endif
+__global__ void __launch_bounds__(128, LQ_PLAQ_MINB) clover_plaq_kernel(Geom g, const df2 *__restrict__ Ue,
                                                           const df2 *__restrict__ Uo, float2 *H)
 {
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
