@@ -77,6 +77,16 @@ __device__ __forceinline__ int tile_row(const unsigned char *par, int j, int p)
     return FULL ? 2 * j + (par[j] != p) : j;
 }
 
+// shared-memory slot of tile row r: with FULL the rows are stored de-interleaved
+// by parity (row r at (r & 1) * TS/2 + r / 2), so that the rows 2j + b that
+// consecutive j read sit in consecutive slots, and TPAD = 13 spreads eight
+// consecutive slots over all eight 16-byte bank groups
+template <bool FULL>
+__device__ __forceinline__ int tile_slot(int r)
+{
+    return FULL ? (r & 1) * (TS / 2) + (r >> 1) : r;
+}
+
 // natural [n][12] c128 -> internal field(s): f0 (FULL: even sites), f1 (odd sites)
 template <int PR, bool FULL>
 __global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *__restrict__ nat,
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *
     const long long n = FULL ? g.V : g.Vh;
     const long long r0 = (long long)blockIdx.x * TS;
     const int rows = (int)(n - r0 < TS ? n - r0 : TS);
-    for (int i = threadIdx.x; i < rows * 12; i += TT) tile[i / 12][i % 12] = __ldg(nat + r0 * 12 + i);
+    for (int i = threadIdx.x; i < rows * 12; i += TT) tile[tile_slot<FULL>(i / 12)][i % 12] = __ldg(nat + r0 * 12 + i);
     if (FULL && threadIdx.x < TS / 2 && 2 * (int)threadIdx.x < rows) par[threadIdx.x] = lex_parity(g, r0 + 2 * threadIdx.x);
     __syncthreads();
     constexpr int NV = Vec<PR>::N, PER = FULL ? TS / 2 : TS;
@@ -98,7 +108,7 @@ __global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *
             const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
             typename Vec<PR>::T *f = p ? f1 : f0;
             f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)] =
-                Vec<PR>::from(tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
+                Vec<PR>::from(tile[tile_slot<FULL>(LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT))], k);
         }
     } else {            // the last, partial tile (rows is even on a full lattice)
         const int per = FULL ? rows / 2 : rows;
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(TT) import_tile_kernel(Geom g, const double2 *
             const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
             typename Vec<PR>::T *f = p ? f1 : f0;
             f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)] =
-                Vec<PR>::from(tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
+                Vec<PR>::from(tile[tile_slot<FULL>(LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT))], k);
         }
     }
 }
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(TT) export_tile_kernel(Geom g, const typename 
             const int j = w % PER, pk = w / PER, p = pk / NV, k = pk % NV;
             const typename Vec<PR>::T *f = p ? f1 : f0;
             Vec<PR>::to(f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)],
-                        tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
+                        tile[tile_slot<FULL>(LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT))], k);
         }
     } else {
         const int per = FULL ? rows / 2 : rows;
@@ -139,11 +149,11 @@ __global__ void __launch_bounds__(TT) export_tile_kernel(Geom g, const typename 
             const int j = w % per, pk = w / per, p = pk / NV, k = pk % NV;
             const typename Vec<PR>::T *f = p ? f1 : f0;
             Vec<PR>::to(f[k * g.stride + LQ_IDX(s0 + j, g.Vh, B_LAYOUT)],
-                        tile[LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT)], k);
+                        tile[tile_slot<FULL>(LQ_IDX(tile_row<FULL>(par, j, p), rows, B_LAYOUT))], k);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * 12; i += TT) nat[r0 * 12 + i] = tile[i / 12][i % 12];
+    for (int i = threadIdx.x; i < rows * 12; i += TT) nat[r0 * 12 + i] = tile[tile_slot<FULL>(i / 12)][i % 12];
 }
 
 // gauge links: U_nat[lex][mu][3][3] c128 -> per parity U64 [mu][9][stride]
